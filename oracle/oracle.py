@@ -1,0 +1,227 @@
+"""numpy front end of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg call this module; the CUDA library never does.  It imports
+nothing from the CUDA package.
+
+All fields are complex128 in the canonical layouts:
+  spinor psi[V, 4, 3]; gauge U[V, 4, 3, 3]; clover C[V, 12, 12] with index
+  spin*3 + colour; force g[V, 4, 3, 3].
+Site s = x + Lx*(y + Ly*(z + Lz*t)).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_i4 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i8 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_c16 = np.ctypeslib.ndpointer(dtype=np.complex128, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.or_gamma.argtypes = [_c16]
+        L.or_sigma.argtypes = [_c16]
+        L.or_threads.restype = C.c_int
+        L.or_field_strength_site.argtypes = [_i4, _c16, C.c_long, _c16]
+        L.or_clover_site.argtypes = [_i4, C.c_double, C.c_double, _c16, C.c_long, _c16]
+        L.or_clover_build.argtypes = [_i4, C.c_double, C.c_double, _c16, _c16]
+        L.or_invert.argtypes = [C.c_int, _c16, _c16]
+        L.or_invert.restype = C.c_int
+        L.or_clover_invert.argtypes = [_i4, _c16, _c16]
+        L.or_clover_invert.restype = C.c_int
+        L.or_dirac.argtypes = [_i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, C.c_int]
+        L.or_dirac_at.argtypes = [_i4, C.c_int, C.c_double, C.c_double, _c16, _c16, C.c_long,
+                                  _i8, _c16, C.c_int]
+        L.or_dirac_block.argtypes = [_i4, _i4, _i4, C.c_double, _c16, _c16, _c16, _c16, C.c_int]
+        L.or_mr_block.argtypes = [_i4, _i4, _i4, C.c_double, _c16, _c16, _c16, _c16, C.c_void_p,
+                                  C.c_int]
+        L.or_sap.argtypes = [_i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, C.c_int, C.c_int]
+        L.or_solve.argtypes = [_i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, C.c_int,
+                               C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                               C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.or_solve.restype = C.c_int
+        L.or_force.argtypes = [_i4, C.c_int, C.c_double, C.c_double, _c16, _c16, _c16, _c16]
+        _lib = L
+    return _lib
+
+
+def _dims(d):
+    return np.ascontiguousarray(np.asarray(d, dtype=np.int32).reshape(4))
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def threads() -> int:
+    """Number of OpenMP threads the oracle uses (1 without OpenMP)."""
+    return int(lib().or_threads())
+
+
+def gamma():
+    """(gamma_x, gamma_y, gamma_z, gamma_t, gamma_5) as a (5, 4, 4) array."""
+    out = np.zeros((5, 4, 4), np.complex128)
+    lib().or_gamma(out)
+    return out
+
+
+def sigma():
+    """sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu] as a (4, 4, 4, 4) array."""
+    out = np.zeros((4, 4, 4, 4), np.complex128)
+    lib().or_sigma(out)
+    return out
+
+
+def field_strength_site(dims, U, site):
+    """F_{mu nu}(x) for the planes (01, 02, 03, 12, 13, 23), shape (6, 3, 3)."""
+    out = np.zeros((6, 3, 3), np.complex128)
+    lib().or_field_strength_site(_dims(dims), _c(U), int(site), out)
+    return out
+
+
+def clover_site(dims, kappa, csw, U, site):
+    out = np.zeros((12, 12), np.complex128)
+    lib().or_clover_site(_dims(dims), float(kappa), float(csw), _c(U), int(site), out)
+    return out
+
+
+def clover(dims, kappa, csw, U):
+    """C(x) = 1 + i kappa c_SW sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x), (V, 12, 12)."""
+    V = int(np.prod(dims))
+    out = np.zeros((V, 12, 12), np.complex128)
+    lib().or_clover_build(_dims(dims), float(kappa), float(csw), _c(U), out)
+    return out
+
+
+def invert(A):
+    A = _c(A)
+    n = A.shape[0]
+    out = np.zeros_like(A)
+    if lib().or_invert(n, A, out) != 0:
+        raise ZeroDivisionError("singular matrix")
+    return out
+
+
+def clover_inverse(dims, Cl):
+    out = np.zeros_like(_c(Cl))
+    if lib().or_clover_invert(_dims(dims), _c(Cl), out) != 0:
+        raise ZeroDivisionError("singular clover block")
+    return out
+
+
+def dirac(dims, tbc, kappa, U, Cl, psi, dagger=False):
+    """D psi (or D^dagger psi) on the whole lattice; psi (V, 4, 3)."""
+    psi = _c(psi)
+    out = np.zeros_like(psi)
+    lib().or_dirac(_dims(dims), int(tbc), float(kappa), _c(U), _c(Cl), psi, out, int(bool(dagger)))
+    return out
+
+
+def dirac_at(dims, tbc, kappa, csw, U, psi, sites, dagger=False):
+    """D psi at the listed sites only (clover built on the fly); (n, 4, 3)."""
+    sites = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
+    out = np.zeros((len(sites), 4, 3), np.complex128)
+    lib().or_dirac_at(_dims(dims), int(tbc), float(kappa), float(csw), _c(U), _c(psi),
+                      len(sites), sites, out, int(bool(dagger)))
+    return out
+
+
+def block_sites(dims, bdims, bc):
+    """Global sites of block bc in local lexicographic order."""
+    bdims = [int(b) for b in bdims]
+    out = []
+    for lt in range(bdims[3]):
+        for lz in range(bdims[2]):
+            for ly in range(bdims[1]):
+                for lx in range(bdims[0]):
+                    c = [bc[0] * bdims[0] + lx, bc[1] * bdims[1] + ly,
+                         bc[2] * bdims[2] + lz, bc[3] * bdims[3] + lt]
+                    out.append(c[0] + dims[0] * (c[1] + dims[1] * (c[2] + dims[2] * c[3])))
+    return np.array(out, dtype=np.int64)
+
+
+def dirac_block(dims, bdims, bc, kappa, U, Cl, v, dagger=False):
+    """Dirichlet block operator D_B on a block vector v (V_B, 4, 3)."""
+    v = _c(v)
+    out = np.zeros_like(v)
+    lib().or_dirac_block(_dims(dims), _dims(bdims), _dims(bc), float(kappa), _c(U), _c(Cl), v,
+                         out, int(bool(dagger)))
+    return out
+
+
+def mr_block(dims, bdims, bc, kappa, U, Cl, r, nmr, return_residual=False):
+    """k = nmr minimal-residual steps on D_B e = r from e = 0."""
+    r = _c(r)
+    e = np.zeros_like(r)
+    rout = np.zeros_like(r) if return_residual else None
+    lib().or_mr_block(_dims(dims), _dims(bdims), _dims(bc), float(kappa), _c(U), _c(Cl), r, e,
+                      None if rout is None else rout.ctypes.data, int(nmr))
+    return (e, rout) if return_residual else e
+
+
+def sap(dims, bdims, tbc, kappa, U, Cl, b, x0=None, ncy=4, nmr=4):
+    """n_cy multiplicative SAP sweeps on D x = b; returns the updated x."""
+    b = _c(b)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128, copy=True)
+    lib().or_sap(_dims(dims), _dims(bdims), int(tbc), float(kappa), _c(U), _c(Cl), b, x,
+                 int(ncy), int(nmr))
+    return x
+
+
+def solve(dims, bdims, tbc, kappa, U, Cl, b, method="fgcr", precond="sap", ncy=4, nmr=4,
+          m=16, tol=1e-10, max_iter=1000, x0=None):
+    """Solve D x = b.  Returns (x, status, iterations, true relative residual)."""
+    b = _c(b)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128, copy=True)
+    it = C.c_int(0)
+    res = C.c_double(0)
+    st = lib().or_solve(_dims(dims), _dims(bdims), int(tbc), float(kappa), _c(U), _c(Cl), b, x,
+                        {"fgcr": 0, "fbicgstab": 1}[method], {"none": 0, "sap": 1}[precond],
+                        int(ncy), int(nmr), int(m), float(tol), int(max_iter), C.byref(it),
+                        C.byref(res))
+    return x, int(st), int(it.value), float(res.value)
+
+
+def gamma5(psi):
+    """gamma_5 = diag(1, 1, -1, -1) on the spin index."""
+    out = np.array(psi, dtype=np.complex128, copy=True)
+    out[..., 2:, :] *= -1
+    return out
+
+
+def force(dims, tbc, kappa, csw, U, X, Y):
+    """dS/dRe U + i dS/dIm U for S = ||Y||^2, Y = D^-dagger phi, X = D^-1 Y."""
+    V = int(np.prod(dims))
+    g = np.zeros((V, 4, 3, 3), np.complex128)
+    lib().or_force(_dims(dims), int(tbc), float(kappa), float(csw), _c(U), _c(X), _c(Y), g)
+    return g
+
+
+def force_solves(dims, bdims, tbc, kappa, U, Cl, phi, tol=1e-13, **kw):
+    """Y = D^-dagger phi (as gamma5 D^-1 gamma5 phi) and X = D^-1 Y."""
+    y5, st1, _, _ = solve(dims, bdims, tbc, kappa, U, Cl, gamma5(phi), tol=tol, **kw)
+    Y = gamma5(y5)
+    X, st2, _, _ = solve(dims, bdims, tbc, kappa, U, Cl, Y, tol=tol, **kw)
+    if st1 or st2:
+        raise RuntimeError("oracle solve did not converge")
+    return X, Y
+
+
+def action(dims, bdims, tbc, kappa, csw, U, phi, tol=1e-13, **kw):
+    """S = phi^dagger (D^dagger D)^-1 phi, evaluated as 2 Re(phi^dagger X) - ||D X||^2,
+    whose error is second order in the solver error of X."""
+    Cl = clover(dims, kappa, csw, U)
+    X, Y = force_solves(dims, bdims, tbc, kappa, U, Cl, phi, tol=tol, **kw)
+    DX = dirac(dims, tbc, kappa, U, Cl, X)
+    return 2.0 * np.real(np.vdot(phi, X)) - np.real(np.vdot(DX, DX))
