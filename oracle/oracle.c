@@ -453,8 +453,8 @@ static long block_site(const int *L, const int *Bd, const int *bc, long l)
  * lexicographic order): every hop whose unwrapped target coordinate leaves the
  * block is dropped.  No boundary sign can arise inside a block.
  */
-void or_dirac_block(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U,
-                    const cplx *C, const cplx *in_b, cplx *out_b, int dagger)
+static void dirac_block_impl(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U,
+                             const cplx *C, int compact, const cplx *in_b, cplx *out_b, int dagger)
 {
     init_gamma();
     long VB = block_volume(Bd);
@@ -463,7 +463,7 @@ void or_dirac_block(const int *L, const int *Bd, const int *bc, double kappa, co
         int lc[4];
         long t = l;
         for (int mu = 0; mu < 4; ++mu) { lc[mu] = (int)(t % Bd[mu]); t /= Bd[mu]; }
-        const cplx *Cx = C + x * 144;
+        const cplx *Cx = C + (compact ? l : x) * 144;
         cplx acc[12];
         for (int i = 0; i < 12; ++i) {
             cplx a = 0;
@@ -509,8 +509,14 @@ static double vnorm2(long n, const cplx *a)
  * alpha = <p, r>/<p, p> (<a, b> = a^dagger b; alpha = 0 if <p, p> = 0),
  * e += alpha r, r -= alpha p.  r_out (optional) receives the final residual.
  */
-void or_mr_block(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U,
-                 const cplx *C, const cplx *r_b, cplx *e_b, cplx *r_out, int nmr)
+void or_dirac_block(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U,
+                    const cplx *C, const cplx *in_b, cplx *out_b, int dagger)
+{
+    dirac_block_impl(L, Bd, bc, kappa, U, C, 0, in_b, out_b, dagger);
+}
+
+static void mr_block_impl(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U,
+                          const cplx *C, int compact, const cplx *r_b, cplx *e_b, cplx *r_out, int nmr)
 {
     long n = block_volume(Bd) * 12;
     cplx *r = malloc(sizeof(cplx) * n);
@@ -518,7 +524,7 @@ void or_mr_block(const int *L, const int *Bd, const int *bc, double kappa, const
     memcpy(r, r_b, sizeof(cplx) * n);
     for (long i = 0; i < n; ++i) e_b[i] = 0;
     for (int k = 0; k < nmr; ++k) {
-        or_dirac_block(L, Bd, bc, kappa, U, C, r, p, 0);
+        dirac_block_impl(L, Bd, bc, kappa, U, C, compact, r, p, 0);
         cplx pr = vdot(n, p, r);
         double pp = vnorm2(n, p);
         cplx alpha = (pp > 0) ? pr / pp : 0;
@@ -530,6 +536,24 @@ void or_mr_block(const int *L, const int *Bd, const int *bc, double kappa, const
     if (r_out) memcpy(r_out, r, sizeof(cplx) * n);
     free(r);
     free(p);
+}
+
+void or_mr_block(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U,
+                 const cplx *C, const cplx *r_b, cplx *e_b, cplx *r_out, int nmr)
+{
+    mr_block_impl(L, Bd, bc, kappa, U, C, 0, r_b, e_b, r_out, nmr);
+}
+
+/* the same MR on one block with the block's clover built on the fly from U
+ * (for lattices whose full clover field is too large to hold) */
+void or_mr_block_at(const int *L, const int *Bd, const int *bc, double kappa, double csw,
+                    const cplx *U, const cplx *r_b, cplx *e_b, int nmr)
+{
+    long VB = block_volume(Bd);
+    cplx *Cb = malloc(sizeof(cplx) * VB * 144);
+    for (long l = 0; l < VB; ++l) or_clover_site(L, kappa, csw, U, block_site(L, Bd, bc, l), Cb + l * 144);
+    mr_block_impl(L, Bd, bc, kappa, U, Cb, 1, r_b, e_b, NULL, nmr);
+    free(Cb);
 }
 
 /*

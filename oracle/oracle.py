@@ -46,6 +46,8 @@ def lib():
         L.or_dirac_block.argtypes = [_i4, _i4, _i4, C.c_double, _c16, _c16, _c16, _c16, C.c_int]
         L.or_mr_block.argtypes = [_i4, _i4, _i4, C.c_double, _c16, _c16, _c16, _c16, C.c_void_p,
                                   C.c_int]
+        L.or_mr_block_at.argtypes = [_i4, _i4, _i4, C.c_double, C.c_double, _c16, _c16, _c16,
+                                     C.c_int]
         L.or_sap.argtypes = [_i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, C.c_int, C.c_int]
         L.or_solve.argtypes = [_i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, C.c_int,
                                C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
@@ -168,6 +170,15 @@ def mr_block(dims, bdims, bc, kappa, U, Cl, r, nmr, return_residual=False):
     lib().or_mr_block(_dims(dims), _dims(bdims), _dims(bc), float(kappa), _c(U), _c(Cl), r, e,
                       None if rout is None else rout.ctypes.data, int(nmr))
     return (e, rout) if return_residual else e
+
+
+def mr_block_at(dims, bdims, bc, kappa, csw, U, r, nmr):
+    """MR on one block with its clover built on the fly (no full clover field)."""
+    r = _c(r)
+    e = np.zeros_like(r)
+    lib().or_mr_block_at(_dims(dims), _dims(bdims), _dims(bc), float(kappa), float(csw), _c(U), r, e,
+                         int(nmr))
+    return e
 
 
 def sap(dims, bdims, tbc, kappa, U, Cl, b, x0=None, ncy=4, nmr=4):

@@ -409,3 +409,17 @@ def test_force_matches_central_differences(csw):
               - O.action(dims, bd, tbc, kappa, csw, pert(-h), phi)) / (2 * h)
         an = np.real(np.sum(np.conj(g[site, mu]) * dU))
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * np.abs(g).max()), (site, mu, kind, fd, an)
+
+
+def test_mr_block_at_equals_mr_block():
+    """The on-the-fly-clover MR used for sampled large-lattice checks is the same
+    computation as MR with the stored clover field."""
+    dims, bd = (8, 8, 4, 8), (4, 4, 2, 4)
+    kappa, csw = 0.1355, 1.0
+    U = synth.gauge_field(dims, 0.4, 81)
+    Cl = O.clover(dims, kappa, csw, U)
+    r = synth.gaussian_spinor(bd, 82)
+    for bc in [(0, 1, 1, 0), (1, 1, 0, 1)]:
+        a = O.mr_block(dims, bd, bc, kappa, U, Cl, r, 4)
+        b = O.mr_block_at(dims, bd, bc, kappa, csw, U, r, 4)
+        assert np.array_equal(a, b)
