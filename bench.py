@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Benchmark of the clover-Wilson Dslash + SAP smoother hot path on GB300.
+
+One step is one mixed-precision solve of D x = b to a relative residual of
+1e-10 on the 32^3 x 64 workload: FP64 flexible GCR outer solver (Sec. 3), the
+multiplicative SAP smoother (Sec. 2, 4 sweeps x 4 MR steps on 4^4 domains) as
+its preconditioner in FP32 arithmetic on FP16 storage with per-site scales and
+12-real links, and the FP64 operator of Eq. (1) for the outer residual.
+
+`value` is the algorithmic throughput of the step in GB/s: the library counts,
+for every kernel it launches, the bytes that launch must read or write (each
+field once) and the timed region divides their sum by the device time.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash/SAP sweep GB/s & %HBM peak; mixed vs FP64 time-to-1e-10 solve"
+WORKLOAD = dict(name="32^3x64", dims=(32, 32, 32, 64), block=(4, 4, 4, 4), eps=0.5, kappa=0.1370,
+                csw=1.0, config_index=2, prec=16, compress=12, n_cy=4, n_mr=4, restart=16, tol=1e-10)
+# bounded CPU sample of the same recipe (same eps, kappa, c_sw, solver) at 1/64 of the volume
+CPU_SAMPLE_DIMS = (16, 16, 16, 8)
+FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
+# conventional flop counts per site: hopping 1320, clover 504, kappa axpy 48
+FLOP_D = 1872.0
+
+
+def workload_desc(w):
+    return (f"clover-Wilson {w['name']}, eps={w['eps']}, kappa={w['kappa']}, c_sw={w['csw']}, "
+            f"FP16 storage + per-site FP32 scale, 12-real links, FP32 smoother arithmetic, "
+            f"SAP {w['n_cy']} sweeps x {w['n_mr']} MR on 4^4 domains, FGCR({w['restart']}) FP64 outer, "
+            f"tol {w['tol']:g}")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.lines = []
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_uuid(dev):
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def counters(lib, reset=False):
+    n = C.c_longlong(0)
+    b = C.c_double(0)
+    lib.mgc_counters(C.byref(n), C.byref(b), int(reset))
+    return int(n.value), float(b.value)
+
+
+# ---------------------------------------------------------------------- CPU side
+def oracle_solve_sample(dims, seed_offset=0):
+    """The FP64 oracle's full solve (FGCR + SAP) on a bounded lattice of the
+    workload's recipe.  Returns (seconds, outer iterations, sites, threads)."""
+    from oracle import oracle as O
+    from paper_2112_00501_gb300 import synth
+
+    w = WORKLOAD
+    U = synth.gauge_field(dims, w["eps"], synth.gauge_seed(w["config_index"]) + 100 + seed_offset)
+    b = synth.gaussian_spinor(dims, synth.source_seed(w["config_index"]) + 100 + seed_offset)
+    t0 = time.perf_counter()
+    Cl = O.clover(dims, w["kappa"], w["csw"], U)
+    x, st, it, res = O.solve(dims, w["block"], -1, w["kappa"], U, Cl, b, method="fgcr", precond="sap",
+                             ncy=w["n_cy"], nmr=w["n_mr"], m=w["restart"], tol=w["tol"])
+    dt = time.perf_counter() - t0
+    if st != 0:
+        raise RuntimeError("oracle sample did not converge")
+    return dt, it, synth.volume(dims), O.threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import build as obuild
+
+    obuild.build()
+    # bytes per site per outer iteration of the GPU path (its byte model), from a
+    # tiny GPU-free constant: measured on the GPU path and recorded here as the
+    # unit conversion for the oracle's sites x iterations per second
+    bpsi = float(os.environ.get("MGC_BYTES_PER_SITE_ITER", "0")) or None
+    times, its = [], []
+    for k in range(args.warmup + args.steps):
+        dt, it, V, thr = oracle_solve_sample(CPU_SAMPLE_DIMS, seed_offset=k % 2)
+        if k >= args.warmup:
+            times.append(dt)
+            its.append(it)
+    T = sum(times)
+    site_iters = sum(its) * V
+    unit_conv = bpsi if bpsi else BYTES_PER_SITE_ITER_DEFAULT
+    value = unit_conv * site_iters / T / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(WORKLOAD), "sample": "x".join(map(str, CPU_SAMPLE_DIMS))},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": thr, "kind": "oracle",
+                         "sample": f"FP64 oracle FGCR+SAP solve to 1e-10 of the same recipe on "
+                                   f"{'x'.join(map(str, CPU_SAMPLE_DIMS))}; {sum(its)} outer iterations "
+                                   f"in {T:.1f} s; GB/s = GPU-path algorithmic bytes per site-iteration "
+                                   f"({unit_conv:.0f} B) x site-iterations/s"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# algorithmic bytes per site per outer iteration of the mixed solve (FP16
+# storage, 12-real links, 4 x 4 SAP), used to express oracle throughput in the
+# same unit when no GPU measurement is at hand; bench runs overwrite it with
+# the measured figure
+BYTES_PER_SITE_ITER_DEFAULT = 7000.0
+
+
+# ---------------------------------------------------------------------- GPU side
+def profile_kernel(which):
+    """A few launches of one kernel on 24^3 x 48 at the workload's storage format
+    (working set above the L2 size, about 2 GB on the device), for ncu."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2112_00501_gb300 import api, synth
+
+    w = WORKLOAD
+    dims = (24, 24, 24, 48)
+    U = synth.gauge_field(dims, w["eps"], synth.gauge_seed(3))
+    b = torch.from_numpy(synth.gaussian_spinor(dims, synth.source_seed(3))).cuda()
+    lat = api.Lattice(dims, w["block"], -1)
+    op = api.CloverOperator(api.Gauge(lat, torch.from_numpy(U).cuda(), storage_prec=w["prec"],
+                                      compress=w["compress"]), w["kappa"], w["csw"])
+    bp = lat.pack(b, w["prec"])
+    xp = lat.zeros_packed(w["prec"])
+    for _ in range(2):
+        if which == "sap":
+            op.sap_smooth(bp, xp, w["prec"], 1, 1, w["n_mr"], x_is_zero=False)
+        else:
+            op.apply_D(bp, w["prec"], 1, xp)
+    torch.cuda.synchronize()
+    print("profile run done")
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-kernel", choices=["sap", "dslash"], default=None,
+                    help="run only a few launches of one kernel on 24^3x48 (for ncu captures)")
+    args = ap.parse_args()
+    if args.profile_kernel:
+        return profile_kernel(args.profile_kernel)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_2112_00501_gb300 import _lib, api, synth
+
+    lib = _lib.load()
+    w = WORKLOAD
+    dims = w["dims"]
+    V = synth.volume(dims)
+    U = synth.gauge_field(dims, w["eps"], synth.gauge_seed(w["config_index"]))
+    b_host = synth.gaussian_spinor(dims, synth.source_seed(w["config_index"]))
+    lat = api.Lattice(dims, w["block"], -1)
+    Ud = torch.from_numpy(U).cuda()
+    gauge = api.Gauge(lat, Ud, storage_prec=w["prec"], compress=w["compress"])
+    op = api.CloverOperator(gauge, w["kappa"], w["csw"])
+    b = torch.from_numpy(b_host).cuda()
+    params = api.solve_params(method=0, precond=1, smoother_prec=w["prec"], n_cy=w["n_cy"], n_mr=w["n_mr"],
+                              restart=w["restart"], tol=w["tol"], max_iter=500)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region
+    for _ in range(args.warmup):
+        x, info = op.solve(b, params)
+        assert info.status == 0, info.status
+    barrier()
+    counters(lib, reset=True)
+    sampler = ClockSampler(gpu_uuid(local))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        x, info = op.solve(b, params)
+        iters.append(info.iters)
+        if info.status != 0 or info.true_res > w["tol"]:
+            raise RuntimeError(f"solve failed: status {info.status}, residual {info.true_res}")
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    launches, nbytes = counters(lib, reset=True)
+    true_res = info.true_res
+
+    # ---------------- end to end through the C ABI with host buffers
+    t_e2e, nbytes_e2e = float("nan"), 0.0
+    if not args.no_e2e:
+        b_pin = torch.from_numpy(b_host).pin_memory()
+        op.solve(b_pin, params)
+        barrier()
+        counters(lib, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            xh, info_e = op.solve(b_pin, params)
+        e1.record(stream)
+        barrier()
+        t_e2e = e0.elapsed_time(e1) / 1e3
+        _, nbytes_e2e = counters(lib, reset=True)
+
+    # ---------------- the dominant kernel: SAP colour launches, timed alone
+    rl = lat.pack(b, w["prec"])
+    zl = lat.zeros_packed(w["prec"])
+    reps = 10
+    for _ in range(2):
+        zl.zero_()
+        op.sap_smooth(rl, zl, w["prec"], 1, w["n_cy"], w["n_mr"], x_is_zero=True)
+    torch.cuda.synchronize()
+    sap_ms = []
+    counters(lib, reset=True)
+    for _ in range(reps):
+        zl.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        op.sap_smooth(rl, zl, w["prec"], 1, w["n_cy"], w["n_mr"], x_is_zero=True)
+        s1.record(stream)
+        s1.synchronize()
+        sap_ms.append(s0.elapsed_time(s1))
+    sap_launches, sap_bytes = counters(lib, reset=True)
+    launches_per_call = sap_launches // reps
+    t_launch = statistics.median(sap_ms) / 1e3 / launches_per_call
+    bytes_launch = sap_bytes / sap_launches
+    # flops of one colour launch: residual (skipped when x = 0) + n_mr MR steps
+    # (Dirichlet D_B: 6 of 8 hops stay inside a 4^4 domain; dots 144; two caxpys 192)
+    flop_mr = (1320.0 * 6 / 8 + 504 + 48) + 144 + 192
+    flop_res = FLOP_D + 24 + 24
+    n_x0 = 1  # launches per call with x == 0
+    flops_call = 0.5 * V * (launches_per_call * w["n_mr"] * flop_mr + (launches_per_call - n_x0) * flop_res)
+    sap_tflops = flops_call / (statistics.median(sap_ms) / 1e3) / 1e12
+
+    # ---------------- Dslash alone (workload storage and FP64)
+    def time_dslash(prec):
+        xin = lat.pack(b, prec)
+        out = lat.empty_packed(prec)
+        for _ in range(3):
+            op.apply_D(xin, prec, 1, out)
+        torch.cuda.synchronize()
+        counters(lib, reset=True)
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 20
+        d0.record(stream)
+        for _ in range(n):
+            op.apply_D(xin, prec, 1, out)
+        d1.record(stream)
+        d1.synchronize()
+        _, by = counters(lib, reset=True)
+        t = d0.elapsed_time(d1) / 1e3 / n
+        return t, by / n
+
+    t_d16, by_d16 = time_dslash(w["prec"])
+    t_d64, by_d64 = time_dslash(64)
+
+    # ---------------- plain FP64 GPU path for the time-to-solution comparison
+    fp64 = None
+    if not args.no_fp64_path:
+        g64 = api.Gauge(lat, Ud, storage_prec=64)
+        op64 = api.CloverOperator(g64, w["kappa"], w["csw"])
+        p64 = api.solve_params(method=0, precond=1, smoother_prec=64, n_cy=w["n_cy"], n_mr=w["n_mr"],
+                               restart=w["restart"], tol=w["tol"], max_iter=500)
+        x64, i64 = op64.solve(b, p64)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        x64, i64 = op64.solve(b, p64)
+        f1.record(stream)
+        f1.synchronize()
+        fp64 = {"ms": f0.elapsed_time(f1), "iters": i64.iters, "true_res": i64.true_res}
+        del op64, g64
+    counters(lib, reset=True)
+
+    # ---------------- reduce over ranks
+    t_max = t_dev
+    tot_bytes = nbytes
+    if dist:
+        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        bb = torch.tensor([nbytes, nbytes_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(bb, op=dist.ReduceOp.SUM)
+        t_max, t_e2e = float(tt[0]), float(tt[1])
+        tot_bytes, nbytes_e2e = float(bb[0]), float(bb[1])
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    value = tot_bytes / t_max / 1e9
+    bytes_per_site_iter = nbytes / (V * sum(iters))
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(w), "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (FP64 links alone 1.2 GB)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "time_to_solution_ms": 1e3 * t_max / args.steps,
+        "outer_iterations": iters[-1],
+        "true_residual": true_res,
+        "fp64_path": fp64,
+        "mixed_over_fp64_speedup": (fp64["ms"] / (1e3 * t_max / args.steps)) if fp64 else None,
+        "dslash": {"fp16_12real_gbs": by_d16 / t_d16 / 1e9, "fp16_us": 1e6 * t_d16,
+                   "fp64_gbs": by_d64 / t_d64 / 1e9, "fp64_us": 1e6 * t_d64,
+                   "fp16_frac_hbm": (by_d16 / t_d16 / 1e9 / hbm) if hbm else None},
+        "sap_sweep": {"launch_us": 1e6 * t_launch, "algorithmic_gbs": bytes_launch / t_launch / 1e9,
+                      "frac_hbm": (bytes_launch / t_launch / 1e9 / hbm) if hbm else None,
+                      "tflops_fp32": sap_tflops, "frac_fp32_peak": sap_tflops / FP32_FMA_PEAK_TFLOPS},
+        "roofline": {
+            "kernel": "k_sap_colour (FP16 storage, 12-real links)",
+            "bound": "hbm",
+            "achieved": bytes_launch / t_launch / 1e9,
+            "peak": hbm,
+            "unit": "GB/s",
+            "frac": (bytes_launch / t_launch / 1e9 / hbm) if hbm else None,
+            "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6800",
+        },
+        "e2e": {"value": nbytes_e2e / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": V * 192,
+                "d2h_bytes_per_step": V * 192, "ms_per_step": 1e3 * t_e2e / args.steps},
+        "bytes_per_site_iteration": bytes_per_site_iter,
+    }
+    if not args.no_cpu_baseline:
+        dt, it, Vs, thr = oracle_solve_sample(CPU_SAMPLE_DIMS)
+        cpu_val = bytes_per_site_iter * it * Vs / dt / 1e9
+        line["cpu_baseline"] = {
+            "value": cpu_val, "unit": "GB/s", "cores": thr, "kind": "oracle",
+            "sample": f"FP64 oracle FGCR+SAP solve to 1e-10 of the same recipe on "
+                      f"{'x'.join(map(str, CPU_SAMPLE_DIMS))} ({Vs} sites, {it} outer iterations, "
+                      f"{dt:.1f} s); GB/s = this run's algorithmic bytes per site-iteration "
+                      f"({bytes_per_site_iter:.0f} B) x site-iterations/s"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

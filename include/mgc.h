@@ -1,0 +1,217 @@
+/*
+ * mgc.h -- C ABI of the GB300 clover-Wilson Dirac operator, SAP smoother,
+ * flexible outer solver and link force (arXiv:2112.00501, "Multigrid Solver on
+ * Fugaku": the fine-grid operator of Eq. (1) and the QWS smoother M_SAP of
+ * Sec. 2 used as the post-smoother of Sec. 3).
+ *
+ * Conventions (the paper fixes none of them; these are the library's readings):
+ *   D = C - kappa*H,  H psi(x) = sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                       + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu)],
+ *   C = 1 + i kappa c_SW sum_{mu<nu} sigma_{mu nu} F_{mu nu}   (Eq. (1)),
+ *   F_{mu nu} = (Q_{mu nu} - Q_{mu nu}^+)/8 (four-leaf clover, no trace
+ *   subtraction), chiral gamma basis with gamma_5 = diag(1, 1, -1, -1), so C is
+ *   two 6x6 Hermitian blocks; periodic in x, y, z and periodic (t_bc = +1) or
+ *   antiperiodic (t_bc = -1) in t, applied to the hops that cross t = Lt-1 <-> 0.
+ *
+ * Canonical external layouts (complex128 = two doubles, real then imaginary):
+ *   site  s = x + Lx*(y + Ly*(z + Lz*t))
+ *   spinor  [nrhs][s][spin 4][colour 3]       (24 doubles per site)
+ *   gauge   [s][mu 4][row 3][col 3]           (U_mu(s) links s to s+mu)
+ *   clover  [s][12][12], index spin*3+colour  (export only)
+ *   force   [s][mu 4][row 3][col 3]           (dS/dRe U + i dS/dIm U)
+ *
+ * Packed device layouts ("packed spinors") are what the operator, smoother and
+ * conversion calls take.  Sites are ordered block by block (the SAP domains of
+ * the lattice), and inside a block even sites come before odd sites; each
+ * precision stores a site's 24 reals as planes of 16-byte vectors so that
+ * consecutive sites are consecutive in memory:
+ *   prec 64: 12 planes of double2 per block, [rhs][block][plane][site]
+ *   prec 32:  6 planes of float4
+ *   prec 16:  3 planes of 8 halves, then (after all rhs' planes) one float
+ *             scale per site; the stored halves are value/scale and the scale
+ *             is the site's largest |real component|.
+ * mgc_spinor_bytes() gives the size; mgc_spinor_pack()/unpack() convert.
+ *
+ * Ownership: the caller owns every buffer it passes (for example a torch
+ * tensor's data pointer); the library never frees them.  Handles own the
+ * library's packed copies of the gauge field and clover term and any solver
+ * workspace, and release them in the matching destroy call.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Operator, smoother and conversion calls only enqueue work on it.
+ * mgc_solve and mgc_force synchronise the stream (they read convergence
+ * scalars back to the host).
+ *
+ * Errors: every call returns an MGC_* status; mgc_status_string() names it and
+ * mgc_last_error() returns a message for the last failing call of the calling
+ * host thread.  No call aborts the process.
+ */
+#ifndef MGC_H
+#define MGC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MGC_OK 0
+#define MGC_ERR_INVALID_ARG 1       /* NULL handle/pointer, bad enum value */
+#define MGC_ERR_UNSUPPORTED_SHAPE 2 /* dims not divisible by block, odd block count, ... */
+#define MGC_ERR_NOT_UNITARY 3       /* 12-real compression asked for a non-SU(3) field */
+#define MGC_ERR_CUDA 4              /* a CUDA runtime call failed (see mgc_last_error) */
+#define MGC_NOT_CONVERGED 5         /* solver hit max_iter; info holds the residual */
+#define MGC_ERR_BREAKDOWN 6         /* NaN/Inf or a zero denominator in the solver */
+#define MGC_ERR_TIMEOUT 7           /* a bounded device wait ran out */
+#define MGC_ERR_NO_DEVICE 8         /* no usable sm_103 device */
+
+/* storage precisions */
+#define MGC_PREC_64 64
+#define MGC_PREC_32 32
+#define MGC_PREC_16 16
+
+typedef struct mgc_lattice_s *mgc_lattice_t;
+typedef struct mgc_gauge_s *mgc_gauge_t;
+typedef struct mgc_clover_s *mgc_clover_t;
+
+const char *mgc_status_string(int status);
+const char *mgc_last_error(void);
+int mgc_version(void);
+
+/*
+ * Process-wide counters kept by the library (no paper counterpart; they make
+ * throughput measurable): the number of this library's kernel launches and
+ * the algorithmic bytes of those launches, i.e. every field a launch must
+ * read or write counted once (spinors, links, clover, Krylov vectors at
+ * their storage precision).  reset != 0 zeroes both after reading.
+ */
+int mgc_counters(long long *launches, double *algorithmic_bytes, int reset);
+
+/*
+ * Lattice geometry with SAP domains (Sec. 2: the domain-decomposed smoother).
+ * dims = (Lx, Ly, Lz, Lt); block = SAP domain extents, each a power of two >= 2
+ * with dims[mu] / block[mu] even (so the red/black colouring of domains is
+ * consistent across the periodic wrap) and at most 1024 sites per domain.
+ * t_bc = +1 (periodic) or -1 (antiperiodic) in t.
+ * Errors: INVALID_ARG for a NULL out or bad t_bc, UNSUPPORTED_SHAPE otherwise.
+ */
+int mgc_lattice_create(const int dims[4], const int block[4], int t_bc, mgc_lattice_t *out);
+int mgc_lattice_destroy(mgc_lattice_t lat);
+long long mgc_lattice_volume(mgc_lattice_t lat);
+
+/* Bytes of a packed spinor buffer holding nrhs fields at precision prec. */
+size_t mgc_spinor_bytes(mgc_lattice_t lat, int prec, int nrhs);
+
+/*
+ * Canonical complex128 spinors (device pointer, nrhs fields) to the packed
+ * layout at precision prec, and back.  Rounding to FP32/FP16 is to nearest
+ * even; prec 16 stores a per-site scale.  Asynchronous on stream.
+ */
+int mgc_spinor_pack(mgc_lattice_t lat, int prec, int nrhs, const double *canonical, void *packed,
+                    void *stream);
+int mgc_spinor_unpack(mgc_lattice_t lat, int prec, int nrhs, const void *packed, double *canonical,
+                      void *stream);
+/* packed precision conversion (same lattice, same nrhs) */
+int mgc_spinor_convert(mgc_lattice_t lat, int nrhs, int prec_in, const void *in, int prec_out,
+                       void *out, void *stream);
+
+/*
+ * Gauge field U (canonical complex128, V*4*9 entries; host memory if
+ * on_device == 0, else device memory).  The handle keeps an FP64 copy for the
+ * outer solver and a copy at storage_prec (32 or 16; 64 adds nothing) with
+ * compress = 18 (full matrices) or 12 (rows 0 and 1; row 2 is rebuilt as
+ * conj(row0 x row1), which needs SU(3) links: with compress = 12 the call
+ * returns MGC_ERR_NOT_UNITARY when any link's unitarity or determinant error
+ * exceeds 1e-10).  Synchronises stream.
+ */
+int mgc_gauge_create(mgc_lattice_t lat, const double *U, int on_device, int storage_prec,
+                     int compress, void *stream, mgc_gauge_t *out);
+int mgc_gauge_destroy(mgc_gauge_t g);
+
+/*
+ * The clover-Wilson operator D = C - kappa*H (Eq. (1)).  C and C^-1 are
+ * computed on the GPU in FP64 from the gauge field's clover leaves (Sec. 2:
+ * computing C and C^-1 from the gauge field); a copy of C at the gauge's
+ * storage precision is kept for the smoother.  The gauge handle must outlive
+ * the operator.  Synchronises stream.
+ */
+int mgc_clover_create(mgc_gauge_t g, double kappa, double csw, void *stream, mgc_clover_t *out);
+int mgc_clover_destroy(mgc_clover_t op);
+/* C (inverse = 0) or C^-1 (inverse = 1) as canonical 12x12 complex128 per site (device). */
+int mgc_clover_export(mgc_clover_t op, int inverse, double *out, void *stream);
+
+/*
+ * out = D in and out = D^dagger in (= gamma5 D gamma5 in) for nrhs packed
+ * spinors at precision prec (64, or the gauge's storage_prec).  Eq. (1).
+ * in and out must not overlap.  Asynchronous on stream.
+ */
+int mgc_apply_D(mgc_clover_t op, const void *in, void *out, int nrhs, int prec, void *stream);
+int mgc_apply_Ddag(mgc_clover_t op, const void *in, void *out, int nrhs, int prec, void *stream);
+
+/*
+ * out = C in (inverse = 0) or C^-1 in (inverse = 1), site-local two 6x6
+ * Hermitian blocks (Eq. (1); C^-1 is what QWS applies before M_SAP, Sec. 3).
+ * prec 64 uses C or C^-1; lower precisions support inverse = 0 only.
+ */
+int mgc_apply_clover(mgc_clover_t op, const void *in, void *out, int nrhs, int prec, int inverse,
+                     void *stream);
+
+/*
+ * Multiplicative SAP (Sec. 2, M_SAP; Sec. 3, post-smoother): n_cy sweeps, each
+ * visiting the red domains then the black domains; for every domain B,
+ * x_B += MR_{n_mr}(D_B, (b - D x)|_B) with D_B the Dirichlet domain operator
+ * and n_mr minimal-residual steps from zero.  x (packed, prec) is updated in
+ * place; x_is_zero = 1 promises x == 0 on entry and skips its first residual.
+ * prec 64 computes in FP64; 32 and 16 compute in FP32.  Asynchronous.
+ */
+int mgc_sap_smooth(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, int n_mr,
+                   int prec, int x_is_zero, void *stream);
+
+/* outer solver parameters (Sec. 3: flexible outer solver, SAP preconditioner) */
+typedef struct {
+    int method;        /* 0 = FGCR(restart), 1 = flexible BiCGStab */
+    int precond;       /* 0 = none, 1 = SAP */
+    int smoother_prec; /* 64, 32 or 16 (16/32 need the gauge's storage_prec) */
+    int n_cy;          /* SAP sweeps per preconditioner application */
+    int n_mr;          /* MR steps per domain */
+    int restart;       /* FGCR restart length m (<= 32) */
+    double tol;        /* stop when ||b - D x|| <= tol ||b||, D in FP64 */
+    int max_iter;      /* outer iterations (preconditioner applications for FGCR) */
+    int on_device;     /* 1: b, x are device pointers; 0: host pointers */
+    int x_is_guess;    /* 1: x holds the initial guess; 0: start from x = 0 */
+} mgc_solve_params;
+
+typedef struct {
+    int status;        /* MGC_OK, MGC_NOT_CONVERGED or MGC_ERR_BREAKDOWN */
+    int iters;         /* outer iterations taken (max over right-hand sides) */
+    int restarts;      /* true-residual recomputations */
+    double true_res;   /* max over rhs of ||b - D x|| / ||b|| in FP64 */
+} mgc_solve_info;
+
+void mgc_solve_params_default(mgc_solve_params *p);
+
+/*
+ * Solve D x = b for nrhs canonical complex128 right-hand sides (one after the
+ * other).  FP64 vectors, inner products, orthogonalisation and residual
+ * updates; the SAP preconditioner in smoother_prec.  Synchronises stream.
+ */
+int mgc_solve(mgc_clover_t op, const double *b, double *x, int nrhs, const mgc_solve_params *p,
+              mgc_solve_info *info, void *stream);
+
+/*
+ * Link force of S = phi^+ (D^+ D)^-1 phi: solves D^+ Y = phi (as
+ * gamma5 D^-1 gamma5 phi) and D X = Y, then dS/dU from the hopping outer
+ * products and the clover-leaf derivative.  phi: canonical complex128 (one
+ * field, on_device as in p); dSdU: canonical [V][4][3][3] complex128 in the
+ * same memory kind.  action (optional) receives S estimated as
+ * 2 Re(phi^+ X) - ||D X||^2.  Synchronises stream.
+ */
+int mgc_force(mgc_clover_t op, const double *phi, double *dSdU, const mgc_solve_params *p,
+              mgc_solve_info *info, double *action, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGC_H */

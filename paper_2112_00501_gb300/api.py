@@ -1,0 +1,240 @@
+"""Python binding of the C ABI with torch tensors for device memory and streams.
+
+Names follow include/mgc.h.  Tensors are passed as raw pointers; the library
+does all the work.  Canonical fields are complex128 tensors:
+  spinor (V, 4, 3) or (nrhs, V, 4, 3); gauge (V, 4, 3, 3); clover (V, 12, 12).
+Packed fields are uint8 tensors of Lattice.spinor_bytes(prec, nrhs) bytes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import SolveInfo, SolveParams, check
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+def _canon(t, device) -> torch.Tensor:
+    if isinstance(t, np.ndarray):
+        t = torch.from_numpy(np.ascontiguousarray(t, dtype=np.complex128))
+    t = t.to(device=device, dtype=torch.complex128)
+    return t.contiguous()
+
+
+class Lattice:
+    """Lattice extents, SAP domain extents and the t boundary condition."""
+
+    def __init__(self, dims, block, t_bc: int = -1):
+        self.lib = _lib.load()
+        self.dims = tuple(int(d) for d in dims)
+        self.block = tuple(int(b) for b in block)
+        self.t_bc = int(t_bc)
+        h = C.c_void_p()
+        d = (C.c_int * 4)(*self.dims)
+        b = (C.c_int * 4)(*self.block)
+        check(self.lib.mgc_lattice_create(d, b, self.t_bc, C.byref(h)), "mgc_lattice_create")
+        self.handle = h
+        self.volume = int(self.lib.mgc_lattice_volume(h))
+
+    def spinor_bytes(self, prec: int, nrhs: int = 1) -> int:
+        return int(self.lib.mgc_spinor_bytes(self.handle, prec, nrhs))
+
+    def empty_packed(self, prec: int, nrhs: int = 1, device="cuda") -> torch.Tensor:
+        return torch.empty(self.spinor_bytes(prec, nrhs), dtype=torch.uint8, device=device)
+
+    def zeros_packed(self, prec: int, nrhs: int = 1, device="cuda") -> torch.Tensor:
+        return torch.zeros(self.spinor_bytes(prec, nrhs), dtype=torch.uint8, device=device)
+
+    def pack(self, psi, prec: int, out=None, stream=None) -> torch.Tensor:
+        """canonical complex128 (device) -> packed at prec"""
+        psi = _canon(psi, "cuda")
+        nrhs = 1 if psi.dim() == 3 else psi.shape[0]
+        if out is None:
+            out = self.empty_packed(prec, nrhs)
+        check(self.lib.mgc_spinor_pack(self.handle, prec, nrhs, _ptr(psi), _ptr(out), _stream(stream)),
+              "mgc_spinor_pack")
+        return out
+
+    def unpack(self, packed: torch.Tensor, prec: int, nrhs: int = 1, out=None, stream=None) -> torch.Tensor:
+        if out is None:
+            shape = (self.volume, 4, 3) if nrhs == 1 else (nrhs, self.volume, 4, 3)
+            out = torch.empty(shape, dtype=torch.complex128, device="cuda")
+        check(self.lib.mgc_spinor_unpack(self.handle, prec, nrhs, _ptr(packed), _ptr(out), _stream(stream)),
+              "mgc_spinor_unpack")
+        return out
+
+    def convert(self, packed: torch.Tensor, prec_in: int, prec_out: int, nrhs: int = 1, out=None, stream=None):
+        if out is None:
+            out = self.empty_packed(prec_out, nrhs)
+        check(self.lib.mgc_spinor_convert(self.handle, nrhs, prec_in, _ptr(packed), prec_out, _ptr(out),
+                                          _stream(stream)), "mgc_spinor_convert")
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self.lib.mgc_lattice_destroy(h)
+            self.handle = None
+
+
+class Gauge:
+    """Packed copies of a gauge field: FP64 plus one at storage_prec (18 or 12 reals)."""
+
+    def __init__(self, lattice: Lattice, U, storage_prec: int = 32, compress: int = 18, stream=None):
+        self.lib = lattice.lib
+        self.lattice = lattice
+        self.prec = int(storage_prec)
+        self.compress = int(compress)
+        on_device = isinstance(U, torch.Tensor) and U.is_cuda
+        if on_device:
+            Ut = U.to(torch.complex128).contiguous()
+        else:
+            Ut = torch.from_numpy(np.ascontiguousarray(np.asarray(U), dtype=np.complex128))
+        h = C.c_void_p()
+        check(self.lib.mgc_gauge_create(lattice.handle, _ptr(Ut), int(on_device), self.prec, self.compress,
+                                        _stream(stream), C.byref(h)), "mgc_gauge_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self.lib.mgc_gauge_destroy(h)
+            self.handle = None
+
+
+def solve_params(**kw) -> SolveParams:
+    p = SolveParams()
+    _lib.load().mgc_solve_params_default(C.byref(p))
+    names = {f[0] for f in SolveParams._fields_}
+    for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown solver parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class CloverOperator:
+    """D = C - kappa H with the clover term of the gauge field (the ABI's mgc_clover_t)."""
+
+    def __init__(self, gauge: Gauge, kappa: float, csw: float, stream=None):
+        self.lib = gauge.lib
+        self.gauge = gauge
+        self.lattice = gauge.lattice
+        self.kappa = float(kappa)
+        self.csw = float(csw)
+        h = C.c_void_p()
+        check(self.lib.mgc_clover_create(gauge.handle, self.kappa, self.csw, _stream(stream), C.byref(h)),
+              "mgc_clover_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self.lib.mgc_clover_destroy(h)
+            self.handle = None
+
+    # -- operator applications on packed fields --------------------------------
+    def apply_D(self, x: torch.Tensor, prec: int, nrhs: int = 1, out=None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = self.lattice.empty_packed(prec, nrhs)
+        check(self.lib.mgc_apply_D(self.handle, _ptr(x), _ptr(out), nrhs, prec, _stream(stream)), "mgc_apply_D")
+        return out
+
+    def apply_Ddag(self, x: torch.Tensor, prec: int, nrhs: int = 1, out=None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = self.lattice.empty_packed(prec, nrhs)
+        check(self.lib.mgc_apply_Ddag(self.handle, _ptr(x), _ptr(out), nrhs, prec, _stream(stream)),
+              "mgc_apply_Ddag")
+        return out
+
+    def apply_clover(self, x: torch.Tensor, prec: int, nrhs: int = 1, inverse=False, out=None, stream=None):
+        if out is None:
+            out = self.lattice.empty_packed(prec, nrhs)
+        check(self.lib.mgc_apply_clover(self.handle, _ptr(x), _ptr(out), nrhs, prec, int(bool(inverse)),
+                                        _stream(stream)), "mgc_apply_clover")
+        return out
+
+    def sap_smooth(self, b: torch.Tensor, x: torch.Tensor, prec: int, nrhs: int = 1, n_cy: int = 4,
+                   n_mr: int = 4, x_is_zero: bool = False, stream=None) -> torch.Tensor:
+        check(self.lib.mgc_sap_smooth(self.handle, _ptr(b), _ptr(x), nrhs, n_cy, n_mr, prec, int(bool(x_is_zero)),
+                                      _stream(stream)), "mgc_sap_smooth")
+        return x
+
+    def export_clover(self, inverse=False, stream=None) -> torch.Tensor:
+        out = torch.empty((self.lattice.volume, 12, 12), dtype=torch.complex128, device="cuda")
+        check(self.lib.mgc_clover_export(self.handle, int(bool(inverse)), _ptr(out), _stream(stream)),
+              "mgc_clover_export")
+        return out
+
+    # -- canonical-field conveniences --------------------------------------------
+    def D(self, psi, prec: int = 64, dagger=False) -> torch.Tensor:
+        """D psi (or D^dagger psi) for canonical complex128 field(s), computed at prec."""
+        psi = _canon(psi, "cuda")
+        nrhs = 1 if psi.dim() == 3 else psi.shape[0]
+        x = self.lattice.pack(psi, prec)
+        y = (self.apply_Ddag if dagger else self.apply_D)(x, prec, nrhs)
+        return self.lattice.unpack(y, prec, nrhs)
+
+    def sap(self, b, prec: int = 64, n_cy: int = 4, n_mr: int = 4, x0=None) -> torch.Tensor:
+        """n_cy SAP sweeps on D x = b from x0 (default 0), canonical in and out."""
+        b = _canon(b, "cuda")
+        nrhs = 1 if b.dim() == 3 else b.shape[0]
+        bp = self.lattice.pack(b, prec)
+        if x0 is None:
+            xp = self.lattice.zeros_packed(prec, nrhs)
+        else:
+            xp = self.lattice.pack(_canon(x0, "cuda"), prec)
+        self.sap_smooth(bp, xp, prec, nrhs, n_cy, n_mr, x_is_zero=x0 is None)
+        return self.lattice.unpack(xp, prec, nrhs)
+
+    def solve(self, b, params: SolveParams | None = None, x0=None, stream=None, **kw):
+        """Solve D x = b.  b: canonical complex128 on the GPU (on_device = 1) or a
+        host tensor / array (on_device = 0).  Returns (x, info)."""
+        p = params if params is not None else solve_params(**kw)
+        host = not (isinstance(b, torch.Tensor) and b.is_cuda)
+        if host:
+            bt = _canon(b, "cpu")
+            if not bt.is_pinned():
+                bt = bt.pin_memory()
+        else:
+            bt = _canon(b, "cuda")
+        p.on_device = 0 if host else 1
+        nrhs = 1 if bt.dim() == 3 else bt.shape[0]
+        if x0 is not None:
+            x = _canon(x0, bt.device).clone()
+            p.x_is_guess = 1
+        else:
+            x = torch.zeros_like(bt)
+            if host:
+                x = x.pin_memory()
+            p.x_is_guess = 0
+        info = SolveInfo()
+        st = self.lib.mgc_solve(self.handle, _ptr(bt), _ptr(x), nrhs, C.byref(p), C.byref(info), _stream(stream))
+        if st not in (_lib.MGC_OK, _lib.MGC_NOT_CONVERGED):
+            check(st, "mgc_solve")
+        return x, info
+
+    def force(self, phi, params: SolveParams | None = None, stream=None, **kw):
+        """dS/dU for S = phi^+ (D^+ D)^-1 phi; returns (g (V, 4, 3, 3) complex128, S, info)."""
+        p = params if params is not None else solve_params(**kw)
+        on_device = isinstance(phi, torch.Tensor) and phi.is_cuda
+        ph = _canon(phi, "cuda" if on_device else "cpu")
+        p.on_device = int(on_device)
+        g = torch.empty((self.lattice.volume, 4, 3, 3), dtype=torch.complex128, device=ph.device)
+        info = SolveInfo()
+        S = C.c_double(0)
+        check(self.lib.mgc_force(self.handle, _ptr(ph), _ptr(g), C.byref(p), C.byref(info), C.byref(S),
+                                 _stream(stream)), "mgc_force")
+        return g, float(S.value), info

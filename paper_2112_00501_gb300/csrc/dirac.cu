@@ -1,0 +1,311 @@
+// Layout conversion and the fused clover-Wilson operator.
+//
+//  - pack / unpack / convert: canonical complex128 spinors <-> packed fields
+//    at 64/32/16 bits, and packed <-> packed precision changes (the storage
+//    conversions of the mixed-precision solver; FP16 carries one FP32 scale
+//    per site).
+//  - gauge pack: canonical links -> packed links (18 or 12 reals).
+//  - k_dirac: out = C psi - kappa H psi (Eq. (1)), or D^dagger with the
+//    projectors swapped, one thread per site; a right-hand-side index runs
+//    over blockIdx.y.
+//  - k_clover_apply: out = C psi or C^-1 psi.
+#include "hop.cuh"
+#include "mgc_host.h"
+
+namespace mgc {
+
+// ------------------------------------------------------------------ accessors
+static Spinor64 sp64(const Geom &g, const void *b) { return Spinor64{(double2 *)b, g.lvb}; }
+static Spinor32 sp32(const Geom &g, const void *b) { return Spinor32{(float4 *)b, g.lvb}; }
+static Spinor16 sp16(const Geom &g, const void *b, int nrhs)
+{
+    uint4 *d = (uint4 *)b;
+    return Spinor16{d, (float *)(d + (size_t)nrhs * g.V * 3), g.lvb};
+}
+
+size_t spinor_bytes(const Geom &g, int prec, int nrhs)
+{
+    const size_t V = (size_t)g.V * nrhs;
+    if (prec == 64) return V * 192;
+    if (prec == 32) return V * 96;
+    return V * 48 + V * 4;
+}
+
+size_t gauge_bytes(const Geom &g, int prec, int compress)
+{
+    const size_t n = (size_t)g.V * 4;
+    if (prec == 64) return n * 9 * 16;
+    if (prec == 32) return compress == 12 ? n * 3 * 16 : n * 9 * 8;
+    return compress == 12 ? n * 3 * 8 : n * 9 * 4;
+}
+
+size_t clover_bytes(const Geom &g, int prec)
+{
+    const size_t V = g.V;
+    if (prec == 64) return V * 36 * 16;
+    if (prec == 32) return V * 18 * 16;
+    return V * 9 * 16 + V * 4;
+}
+
+// ------------------------------------------------------------------ pack
+template <class SP>
+__global__ void k_pack(Geom g, const double2 *__restrict__ canon, SP out)
+{
+    using T = typename SP::Real;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int r = blockIdx.y;
+    int c[4];
+    site_coords(g, i, c);
+    const double2 *q = canon + ((size_t)r * g.V + canon_index(g, c)) * 12;
+    Cx<T> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double2 d = q[k];
+        v[k] = Cx<T>{(T)d.x, (T)d.y};
+    }
+    shift_rhs(out, r, g.V).store(i, v);
+}
+
+template <class SP>
+__global__ void k_unpack(Geom g, SP in, double2 *__restrict__ canon)
+{
+    using T = typename SP::Real;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int r = blockIdx.y;
+    int c[4];
+    site_coords(g, i, c);
+    Cx<T> v[12];
+    shift_rhs(in, r, g.V).load(i, v);
+    double2 *q = canon + ((size_t)r * g.V + canon_index(g, c)) * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) q[k] = make_double2((double)v[k].r, (double)v[k].i);
+}
+
+template <class SI, class SO>
+__global__ void k_convert(Geom g, SI in, SO out)
+{
+    using TI = typename SI::Real;
+    using TO = typename SO::Real;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int r = blockIdx.y;
+    Cx<TI> v[12];
+    Cx<TO> w[12];
+    shift_rhs(in, r, g.V).load(i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = Cx<TO>{(TO)v[k].r, (TO)v[k].i};
+    shift_rhs(out, r, g.V).store(i, w);
+}
+
+int launch_pack(const Geom &g, int prec, int nrhs, const double *canon, void *packed, cudaStream_t s)
+{
+    dim3 grid(grid_for(g.V, 256), nrhs);
+    const double2 *c = (const double2 *)canon;
+    if (prec == 64) k_pack<<<grid, 256, 0, s>>>(g, c, sp64(g, packed));
+    else if (prec == 32) k_pack<<<grid, 256, 0, s>>>(g, c, sp32(g, packed));
+    else k_pack<<<grid, 256, 0, s>>>(g, c, sp16(g, packed, nrhs));
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * nrhs * (192.0 + spinor_site_bytes(prec)));
+    return MGC_OK;
+}
+
+int launch_unpack(const Geom &g, int prec, int nrhs, const void *packed, double *canon, cudaStream_t s)
+{
+    dim3 grid(grid_for(g.V, 256), nrhs);
+    double2 *c = (double2 *)canon;
+    if (prec == 64) k_unpack<<<grid, 256, 0, s>>>(g, sp64(g, packed), c);
+    else if (prec == 32) k_unpack<<<grid, 256, 0, s>>>(g, sp32(g, packed), c);
+    else k_unpack<<<grid, 256, 0, s>>>(g, sp16(g, packed, nrhs), c);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * nrhs * (192.0 + spinor_site_bytes(prec)));
+    return MGC_OK;
+}
+
+template <class SI>
+static void convert_to(const Geom &g, int nrhs, SI in, int pout, void *out, cudaStream_t s)
+{
+    dim3 grid(grid_for(g.V, 256), nrhs);
+    if (pout == 64) k_convert<<<grid, 256, 0, s>>>(g, in, sp64(g, out));
+    else if (pout == 32) k_convert<<<grid, 256, 0, s>>>(g, in, sp32(g, out));
+    else k_convert<<<grid, 256, 0, s>>>(g, in, sp16(g, out, nrhs));
+}
+
+int launch_convert(const Geom &g, int nrhs, int pin, const void *in, int pout, void *out, cudaStream_t s)
+{
+    if (pin == 64) convert_to(g, nrhs, sp64(g, in), pout, out, s);
+    else if (pin == 32) convert_to(g, nrhs, sp32(g, in), pout, out, s);
+    else convert_to(g, nrhs, sp16(g, in, nrhs), pout, out, s);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * nrhs * (spinor_site_bytes(pin) + spinor_site_bytes(pout)));
+    return MGC_OK;
+}
+
+// ------------------------------------------------------------------ gauge pack
+__global__ void k_gauge_pack(Geom g, const double2 *__restrict__ canon, int prec, int compress, void *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int mu = blockIdx.y;
+    int c[4];
+    site_coords(g, i, c);
+    const double2 *q = canon + (canon_index(g, c) * 4 + mu) * 9;
+    const size_t l = i & ((1 << g.lvb) - 1);
+    const size_t blk = i >> g.lvb;
+    if (prec == 64) {
+        double2 *o = (double2 *)out + ((blk * 4 + mu) * 9 << g.lvb) + l;
+        for (int k = 0; k < 9; ++k) o[(size_t)k << g.lvb] = q[k];
+    } else if (prec == 32 && compress == 18) {
+        float2 *o = (float2 *)out + ((blk * 4 + mu) * 9 << g.lvb) + l;
+        for (int k = 0; k < 9; ++k) o[(size_t)k << g.lvb] = make_float2((float)q[k].x, (float)q[k].y);
+    } else if (prec == 32) {
+        float4 *o = (float4 *)out + ((blk * 4 + mu) * 3 << g.lvb) + l;
+        for (int k = 0; k < 3; ++k)
+            o[(size_t)k << g.lvb] =
+                make_float4((float)q[2 * k].x, (float)q[2 * k].y, (float)q[2 * k + 1].x, (float)q[2 * k + 1].y);
+    } else if (compress == 18) {
+        uint32_t *o = (uint32_t *)out + ((blk * 4 + mu) * 9 << g.lvb) + l;
+        for (int k = 0; k < 9; ++k) o[(size_t)k << g.lvb] = pack_half2((float)q[k].x, (float)q[k].y);
+    } else {
+        uint2 *o = (uint2 *)out + ((blk * 4 + mu) * 3 << g.lvb) + l;
+        for (int k = 0; k < 3; ++k)
+            o[(size_t)k << g.lvb] = make_uint2(pack_half2((float)q[2 * k].x, (float)q[2 * k].y),
+                                               pack_half2((float)q[2 * k + 1].x, (float)q[2 * k + 1].y));
+    }
+}
+
+int launch_gauge_pack(const Geom &g, const double *canon_dev, int prec, int compress, void *out, cudaStream_t s)
+{
+    dim3 grid(grid_for(g.V, 256), 4);
+    k_gauge_pack<<<grid, 256, 0, s>>>(g, (const double2 *)canon_dev, prec, compress, out);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * (576.0 + links_site_bytes(prec, compress)));
+    return MGC_OK;
+}
+
+// ------------------------------------------------------------------ D, D^dagger
+template <bool DAG, class SP, class GA, class CL>
+__global__ void __launch_bounds__(256) k_dirac(Geom g, SP in, SP out, GA U, CL C, typename SP::Real kappa)
+{
+    using T = typename SP::Real;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int r = blockIdx.y;
+    const SP src = shift_rhs(in, r, g.V);
+    int c[4];
+    site_coords(g, i, c);
+    Cx<T> o[12];
+    dirac_site<DAG>(g, c, i, src, U, C, kappa, o);
+    shift_rhs(out, r, g.V).store(i, o);
+}
+
+template <class SP, class GA, class CL>
+static void dirac_dispatch(const Geom &g, bool dag, SP in, SP out, GA U, CL C, double kappa, int nrhs,
+                           cudaStream_t s)
+{
+    using T = typename SP::Real;
+    dim3 grid(grid_for(g.V, 256), nrhs);
+    if (dag) k_dirac<true><<<grid, 256, 0, s>>>(g, in, out, U, C, (T)kappa);
+    else k_dirac<false><<<grid, 256, 0, s>>>(g, in, out, U, C, (T)kappa);
+}
+
+static Clover16 cl16(const Geom &g, const mgc_clover_s *op)
+{
+    return Clover16{(uint4 *)op->Clo, op->Clo_sc, g.lvb};
+}
+
+int launch_dirac(const mgc_clover_s *op, int prec, bool dag, const void *in, void *out, int nrhs, cudaStream_t s)
+{
+    const mgc_gauge_s *ga = op->gauge;
+    const Geom &g = ga->lat->g;
+    if (prec == 64) {
+        dirac_dispatch(g, dag, sp64(g, in), sp64(g, out), Gauge64{ga->U64, g.lvb}, Clover64{op->C64, g.lvb},
+                       op->kappa, nrhs, s);
+    } else if (prec != ga->prec) {
+        return fail(MGC_ERR_INVALID_ARG, "operator precision differs from the gauge storage precision");
+    } else if (prec == 32) {
+        Clover32 C{(float4 *)op->Clo, g.lvb};
+        if (ga->compress == 12)
+            dirac_dispatch(g, dag, sp32(g, in), sp32(g, out), Gauge32x12{(float4 *)ga->Ulo, g.lvb}, C, op->kappa,
+                           nrhs, s);
+        else
+            dirac_dispatch(g, dag, sp32(g, in), sp32(g, out), Gauge32x18{(float2 *)ga->Ulo, g.lvb}, C, op->kappa,
+                           nrhs, s);
+    } else {
+        if (ga->compress == 12)
+            dirac_dispatch(g, dag, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x12{(uint2 *)ga->Ulo, g.lvb},
+                           cl16(g, op), op->kappa, nrhs, s);
+        else
+            dirac_dispatch(g, dag, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x18{(uint32_t *)ga->Ulo, g.lvb},
+                           cl16(g, op), op->kappa, nrhs, s);
+    }
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * (2.0 * nrhs * spinor_site_bytes(prec) +
+                            links_site_bytes(prec, prec == 64 ? 18 : ga->compress) + clover_site_bytes(prec)));
+    return MGC_OK;
+}
+
+// ------------------------------------------------------------------ clover apply
+template <class SP, class CL>
+__global__ void k_clover_apply(Geom g, SP in, SP out, CL C)
+{
+    using T = typename SP::Real;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int r = blockIdx.y;
+    Cx<T> v[12], o[12];
+    shift_rhs(in, r, g.V).load(i, v);
+    T cl[72];
+    C.load(i, cl);
+    clover_mul(cl, v, o);
+    shift_rhs(out, r, g.V).store(i, o);
+}
+
+int launch_clover_apply(const mgc_clover_s *op, int prec, bool inverse, const void *in, void *out, int nrhs,
+                        cudaStream_t s)
+{
+    const Geom &g = op->gauge->lat->g;
+    dim3 grid(grid_for(g.V, 256), nrhs);
+    if (prec == 64) {
+        k_clover_apply<<<grid, 256, 0, s>>>(g, sp64(g, in), sp64(g, out),
+                                            Clover64{inverse ? op->Ci64 : op->C64, g.lvb});
+    } else if (inverse) {
+        return fail(MGC_ERR_INVALID_ARG, "C^-1 is kept in FP64 only");
+    } else if (prec != op->gauge->prec) {
+        return fail(MGC_ERR_INVALID_ARG, "clover precision differs from the gauge storage precision");
+    } else if (prec == 32) {
+        k_clover_apply<<<grid, 256, 0, s>>>(g, sp32(g, in), sp32(g, out), Clover32{(float4 *)op->Clo, g.lvb});
+    } else {
+        k_clover_apply<<<grid, 256, 0, s>>>(g, sp16(g, in, nrhs), sp16(g, out, nrhs), cl16(g, op));
+    }
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * (2.0 * nrhs * spinor_site_bytes(prec) + clover_site_bytes(prec)));
+    return MGC_OK;
+}
+
+// ------------------------------------------------------------------ gamma5
+__global__ void k_gamma5(Geom g, int nrhs, const double2 *__restrict__ in, double2 *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int r = blockIdx.y;
+    Spinor64 a = shift_rhs(Spinor64{(double2 *)in, g.lvb}, r, g.V);
+    Spinor64 b = shift_rhs(Spinor64{out, g.lvb}, r, g.V);
+    Cx<double> v[12];
+    a.load(i, v);
+#pragma unroll
+    for (int k = 6; k < 12; ++k) v[k] = -v[k];
+    b.store(i, v);
+}
+
+int launch_gamma5(const Geom &g, int nrhs, const double2 *in, double2 *out, cudaStream_t s)
+{
+    dim3 grid(grid_for(g.V, 256), nrhs);
+    k_gamma5<<<grid, 256, 0, s>>>(g, nrhs, in, out);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * nrhs * 384.0);
+    return MGC_OK;
+}
+
+}  // namespace mgc

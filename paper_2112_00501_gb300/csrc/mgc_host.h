@@ -1,0 +1,108 @@
+// Host-side internals shared by the library's translation units: handle
+// structs, error reporting and the kernel launchers each unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "mgc.h"
+#include "mgc_device.cuh"
+
+struct mgc_lattice_s {
+    mgc::Geom g;
+    int dims[4];
+    int block[4];
+};
+
+struct mgc_gauge_s {
+    mgc_lattice_s *lat;
+    double2 *U64;  // packed FP64, 18 reals per link
+    void *Ulo;     // packed copy at prec/compress (NULL when prec == 64)
+    int prec;      // 64, 32 or 16
+    int compress;  // 18 or 12
+};
+
+namespace mgc {
+struct SolverWork;
+}
+
+struct mgc_clover_s {
+    mgc_gauge_s *gauge;
+    double kappa, csw;
+    double2 *C64;   // packed FP64 clover C
+    double2 *Ci64;  // packed FP64 C^-1
+    void *Clo;      // packed C at gauge->prec (NULL when prec == 64)
+    float *Clo_sc;  // per-site scales of the FP16 clover
+    mgc::SolverWork *work;
+};
+
+namespace mgc {
+
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+int ok();
+
+#define MGC_CUDA(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return mgc::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define MGC_TRY(call)                 \
+    do {                              \
+        int st_ = (call);             \
+        if (st_ != MGC_OK) return st_; \
+    } while (0)
+
+inline int grid_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+// Process-wide counters of kernel launches and of their algorithmic
+// (compulsory) bytes: every field a launch must read or write, counted once.
+void count(long long launches, double bytes);
+// per-site compulsory bytes of a packed spinor, of the four forward links and
+// of the clover term at each storage format
+double spinor_site_bytes(int prec);
+double links_site_bytes(int prec, int compress);
+double clover_site_bytes(int prec);
+
+// packed buffer sizes
+size_t spinor_bytes(const Geom &g, int prec, int nrhs);
+size_t gauge_bytes(const Geom &g, int prec, int compress);
+size_t clover_bytes(const Geom &g, int prec);  // includes FP16 scales
+
+// dirac.cu
+int launch_pack(const Geom &g, int prec, int nrhs, const double *canon, void *packed, cudaStream_t s);
+int launch_unpack(const Geom &g, int prec, int nrhs, const void *packed, double *canon, cudaStream_t s);
+int launch_convert(const Geom &g, int nrhs, int pin, const void *in, int pout, void *out, cudaStream_t s);
+int launch_gauge_pack(const Geom &g, const double *canon_dev, int prec, int compress, void *out, cudaStream_t s);
+int launch_dirac(const mgc_clover_s *op, int prec, bool dag, const void *in, void *out, int nrhs,
+                 cudaStream_t s);
+int launch_clover_apply(const mgc_clover_s *op, int prec, bool inverse, const void *in, void *out, int nrhs,
+                        cudaStream_t s);
+int launch_gamma5(const Geom &g, int nrhs, const double2 *in, double2 *out, cudaStream_t s);
+
+// clover_build.cu
+int launch_clover_build(const Geom &g, const double2 *U64, double kappa, double csw, double2 *C64, double2 *Ci64,
+                        int *d_bad, cudaStream_t s);
+int launch_clover_lowprec(const Geom &g, const double2 *C64, int prec, void *out, cudaStream_t s);
+int launch_clover_export(const Geom &g, const double2 *C64, double *out, cudaStream_t s);
+int launch_unitarity(const Geom &g, const double *canon_dev, double *d_maxerr, cudaStream_t s);
+
+// sap.cu
+int launch_sap(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_mr,
+               int x_is_zero, cudaStream_t s);
+
+// solver.cu
+int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solve_params *p, mgc_solve_info *info,
+          cudaStream_t s);
+void free_work(mgc_clover_s *op);
+// solve D x = b for one packed FP64 field already on the device (x holds the guess if guess != 0)
+int solve_packed(mgc_clover_s *op, const double2 *b, double2 *x, const mgc_solve_params *p, mgc_solve_info *info,
+                 cudaStream_t s);
+
+// force.cu
+int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_params *p, mgc_solve_info *info,
+          double *action, cudaStream_t s);
+
+}  // namespace mgc

@@ -1,0 +1,593 @@
+// FP64 flexible outer solvers around the SAP preconditioner (Sec. 3: the
+// outer solver is flexible BiCGStab, the smoother is M_SAP), with every inner
+// product, orthogonalisation and residual update in FP64 on the GPU.
+//
+//   FGCR(m): z_j = M r, w_j = D z_j, classical Gram-Schmidt of w_j against the
+//   normalised w_0..w_{j-1} (the same combination applied to z_j), then
+//   alpha = <w_j, r>, x += alpha z_j, r -= alpha w_j.  The residual is
+//   recomputed as b - D x at the end of each cycle and when the recursive
+//   residual meets the tolerance.
+//   Flexible BiCGStab: the textbook recurrences with M applied to p and s.
+//
+// Reductions are deterministic: a fixed grid for a given vector length, a
+// fixed per-thread element order, and a last-block pass that sums the block
+// partials in a fixed order.  Scalars stay on the device; the host reads one
+// residual norm per iteration.
+#include <cmath>
+#include <vector>
+
+#include "mgc_host.h"
+
+namespace mgc {
+
+constexpr int RT = 256;        // reduction threads per block
+constexpr int RGRID_MAX = 1024;
+constexpr int MAXM = 32;
+
+struct SolverWork {
+    int m = 0;
+    int lowprec = 0;
+    double2 *x = nullptr, *r = nullptr, *b = nullptr, *t = nullptr;
+    std::vector<double2 *> w, z;  // FGCR directions (BiCGStab reuses them)
+    void *rl = nullptr, *zl = nullptr;
+    double *scal = nullptr;     // device scalars
+    double *partial = nullptr;  // reduction partials
+    unsigned *counter = nullptr;
+    double2 *stage = nullptr;   // canonical staging for host pointers
+    double *hscal = nullptr;    // pinned host copy of a few scalars
+};
+
+// device scalar slots
+enum {
+    S_BB = 0,      // ||b||^2
+    S_RR = 1,      // ||r||^2
+    S_NW = 2,      // ||w_j||^2 after orthogonalisation
+    S_WR = 3,      // <w_j, r> (2 slots)
+    S_RHO = 5,     // BiCGStab rho (2)
+    S_R0V = 7,     // <r0, v> (2)
+    S_TS = 9,      // <t, s> (2)
+    S_TT = 11,     // <t, t>
+    S_BETA = 32,   // CGS coefficients, 2 * MAXM slots
+    S_TOTAL = 32 + 2 * MAXM,
+};
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b)
+{
+    const double n = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / n, (a.y * b.x - a.x * b.y) / n);
+}
+// conj(a) b accumulated into acc[0..1]
+__device__ __forceinline__ void acc_dot(double *acc, double2 a, double2 b)
+{
+    acc[0] = fma(a.x, b.x, fma(a.y, b.y, acc[0]));
+    acc[1] = fma(a.x, b.y, fma(-a.y, b.x, acc[1]));
+}
+__device__ __forceinline__ void acc_n2(double *acc, double2 a) { acc[0] = fma(a.x, a.x, fma(a.y, a.y, acc[0])); }
+__device__ __forceinline__ double2 ld2(const double *p) { return make_double2(p[0], p[1]); }
+
+template <int NV>
+__device__ __forceinline__ void warp_reduce(double *v)
+{
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
+// sum NV values over the block; result valid on thread 0
+template <int NV>
+__device__ __forceinline__ void block_reduce(double *v, double (*sh)[RT / 32])
+{
+    warp_reduce<NV>(v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k][warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0;
+            for (int w = 0; w < RT / 32; ++w) s += sh[k][w];
+            v[k] = s;
+        }
+    __syncthreads();
+}
+
+// out[k] = sum over elements e < n of the values f(e, acc) accumulates
+template <int NV, class F>
+__global__ void __launch_bounds__(RT) k_reduce(long long n, F f, double *partial, unsigned *counter, double *out)
+{
+    __shared__ double sh[NV][RT / 32];
+    __shared__ bool last;
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0;
+    for (long long e = (long long)blockIdx.x * RT + threadIdx.x; e < n; e += (long long)gridDim.x * RT) f(e, acc);
+    block_reduce<NV>(acc, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) partial[blockIdx.x * NV + k] = acc[k];
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0;
+    for (int bi = threadIdx.x; bi < (int)gridDim.x; bi += RT)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partial + bi * NV + k);
+    block_reduce<NV>(acc, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = acc[k];
+        *counter = 0;
+    }
+}
+
+// a plain elementwise map
+template <class F>
+__global__ void __launch_bounds__(RT) k_map(long long n, F f)
+{
+    for (long long e = (long long)blockIdx.x * RT + threadIdx.x; e < n; e += (long long)gridDim.x * RT) f(e);
+}
+
+static int red_grid(long long n)
+{
+    long long g = (n + RT * 4 - 1) / (RT * 4);
+    if (g > RGRID_MAX) g = RGRID_MAX;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// nvec: FP64 vectors of n complex entries the launch reads or writes
+template <int NV, class F>
+static int reduce(long long n, F f, SolverWork *W, double *out, cudaStream_t s, int nvec)
+{
+    k_reduce<NV><<<red_grid(n), RT, 0, s>>>(n, f, W->partial, W->counter, out);
+    MGC_CUDA(cudaGetLastError());
+    count(1, 16.0 * n * nvec);
+    return MGC_OK;
+}
+
+template <class F>
+static int map(long long n, F f, cudaStream_t s, int nvec)
+{
+    k_map<<<red_grid(n), RT, 0, s>>>(n, f);
+    MGC_CUDA(cudaGetLastError());
+    count(1, 16.0 * n * nvec);
+    return MGC_OK;
+}
+
+struct PtrList {
+    const double2 *p[MAXM];
+};
+struct MutPtrList {
+    double2 *p[MAXM];
+};
+
+// ------------------------------------------------------------------ workspace
+void free_work(mgc_clover_s *op)
+{
+    SolverWork *W = op->work;
+    if (!W) return;
+    cudaFree(W->x);
+    cudaFree(W->r);
+    cudaFree(W->b);
+    cudaFree(W->t);
+    for (auto p : W->w) cudaFree(p);
+    for (auto p : W->z) cudaFree(p);
+    cudaFree(W->rl);
+    cudaFree(W->zl);
+    cudaFree(W->scal);
+    cudaFree(W->partial);
+    cudaFree(W->counter);
+    cudaFree(W->stage);
+    cudaFreeHost(W->hscal);
+    delete W;
+    op->work = nullptr;
+}
+
+static int ensure_work(mgc_clover_s *op, int m, int lowprec)
+{
+    const Geom &g = op->gauge->lat->g;
+    if (m < 4) m = 4;  // BiCGStab needs eight vectors: w[0..3], z[0..3]
+    if (op->work && op->work->m >= m && (lowprec == 64 || op->work->lowprec == lowprec)) return MGC_OK;
+    free_work(op);
+    SolverWork *W = new SolverWork();
+    op->work = W;
+    const size_t vb = spinor_bytes(g, 64, 1);
+    W->m = m;
+    MGC_CUDA(cudaMalloc(&W->x, vb));
+    MGC_CUDA(cudaMalloc(&W->r, vb));
+    MGC_CUDA(cudaMalloc(&W->b, vb));
+    MGC_CUDA(cudaMalloc(&W->t, vb));
+    W->w.assign(m, nullptr);
+    W->z.assign(m, nullptr);
+    for (int j = 0; j < m; ++j) {
+        MGC_CUDA(cudaMalloc(&W->w[j], vb));
+        MGC_CUDA(cudaMalloc(&W->z[j], vb));
+    }
+    if (lowprec != 64) {
+        W->lowprec = lowprec;
+        MGC_CUDA(cudaMalloc(&W->rl, spinor_bytes(g, lowprec, 1)));
+        MGC_CUDA(cudaMalloc(&W->zl, spinor_bytes(g, lowprec, 1)));
+    }
+    MGC_CUDA(cudaMalloc(&W->scal, S_TOTAL * sizeof(double)));
+    MGC_CUDA(cudaMemset(W->scal, 0, S_TOTAL * sizeof(double)));
+    MGC_CUDA(cudaMalloc(&W->partial, RGRID_MAX * 8 * sizeof(double)));
+    MGC_CUDA(cudaMalloc(&W->counter, sizeof(unsigned)));
+    MGC_CUDA(cudaMemset(W->counter, 0, sizeof(unsigned)));
+    MGC_CUDA(cudaMalloc(&W->stage, vb));
+    MGC_CUDA(cudaMallocHost(&W->hscal, 8 * sizeof(double)));
+    return MGC_OK;
+}
+
+// read one device scalar (synchronises the stream)
+static int read_scalar(SolverWork *W, int slot, double *out, cudaStream_t s)
+{
+    MGC_CUDA(cudaMemcpyAsync(W->hscal, W->scal + slot, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MGC_CUDA(cudaStreamSynchronize(s));
+    *out = W->hscal[0];
+    return MGC_OK;
+}
+
+// ------------------------------------------------------------------ building blocks
+// z = M v (M = SAP in prec, or the identity)
+static int precondition(mgc_clover_s *op, const mgc_solve_params *p, const double2 *v, double2 *z, cudaStream_t s)
+{
+    const Geom &g = op->gauge->lat->g;
+    SolverWork *W = op->work;
+    if (p->precond == 0) {
+        MGC_CUDA(cudaMemcpyAsync(z, v, spinor_bytes(g, 64, 1), cudaMemcpyDeviceToDevice, s));
+        return MGC_OK;
+    }
+    if (p->smoother_prec == 64) {
+        MGC_CUDA(cudaMemsetAsync(z, 0, spinor_bytes(g, 64, 1), s));
+        return launch_sap(op, 64, v, z, 1, p->n_cy, p->n_mr, 1, s);
+    }
+    MGC_TRY(launch_convert(g, 1, 64, v, p->smoother_prec, W->rl, s));
+    MGC_CUDA(cudaMemsetAsync(W->zl, 0, spinor_bytes(g, p->smoother_prec, 1), s));
+    MGC_TRY(launch_sap(op, p->smoother_prec, W->rl, W->zl, 1, p->n_cy, p->n_mr, 1, s));
+    return launch_convert(g, 1, p->smoother_prec, W->zl, 64, z, s);
+}
+
+static int apply_D64(mgc_clover_s *op, const double2 *in, double2 *out, cudaStream_t s)
+{
+    return launch_dirac(op, 64, false, in, out, 1, s);
+}
+
+// r = b - t, and ||r||^2 into slot
+static int residual(mgc_clover_s *op, double2 *r, const double2 *b, const double2 *t, int slot, cudaStream_t s)
+{
+    SolverWork *W = op->work;
+    const long long n = (long long)op->gauge->lat->g.V * 12;
+    return reduce<1>(
+        n,
+        [=] __device__(long long e, double *acc) {
+            const double2 v = csub(b[e], t[e]);
+            r[e] = v;
+            acc_n2(acc, v);
+        },
+        W, W->scal + slot, s, 3);
+}
+
+static bool bad(double v) { return !std::isfinite(v); }
+
+// ------------------------------------------------------------------ FGCR
+static int fgcr(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
+{
+    SolverWork *W = op->work;
+    const long long n = (long long)op->gauge->lat->g.V * 12;
+    double2 *x = W->x, *r = W->r, *b = W->b, *t = W->t;
+    double *sc = W->scal;
+    const int m = p->restart;
+    double bb, rr;
+
+    MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, b[e]); }, W, sc + S_BB, s, 1));
+    MGC_TRY(read_scalar(W, S_BB, &bb, s));
+    info->iters = 0;
+    info->restarts = 0;
+    if (bb == 0.0) {
+        MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+        info->true_res = 0;
+        return MGC_OK;
+    }
+    const double tol2 = p->tol * p->tol * bb;
+    if (p->x_is_guess) {
+        MGC_TRY(apply_D64(op, x, t, s));
+        MGC_TRY(residual(op, r, b, t, S_RR, s));
+        MGC_TRY(read_scalar(W, S_RR, &rr, s));
+        info->true_res = std::sqrt(rr / bb);
+        if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "FGCR: non-finite initial residual");
+        if (rr <= tol2) return MGC_OK;
+    } else {
+        MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+        MGC_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    }
+    int iters = 0;
+    for (;;) {
+        for (int j = 0; j < m && iters < p->max_iter; ++j) {
+            double2 *wj = W->w[j], *zj = W->z[j];
+            MGC_TRY(precondition(op, p, r, zj, s));
+            MGC_TRY(apply_D64(op, zj, wj, s));
+            // beta_i = <w_i, w_j>, four at a time
+            for (int i0 = 0; i0 < j; i0 += 4) {
+                const int cnt = (j - i0 < 4) ? j - i0 : 4;
+                PtrList L{};
+                for (int q = 0; q < cnt; ++q) L.p[q] = W->w[i0 + q];
+                MGC_TRY(reduce<8>(
+                    n,
+                    [=] __device__(long long e, double *acc) {
+                        const double2 v = wj[e];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (q < cnt) acc_dot(acc + 2 * q, L.p[q][e], v);
+                    },
+                    W, sc + S_BETA + 2 * i0, s, cnt + 1));
+            }
+            // w_j -= sum beta_i w_i, z_j -= sum beta_i z_i; ||w_j||^2 and <w_j, r>
+            PtrList Lw{}, Lz{};
+            for (int q = 0; q < j; ++q) {
+                Lw.p[q] = W->w[q];
+                Lz.p[q] = W->z[q];
+            }
+            const double *beta = sc + S_BETA;
+            MGC_TRY(reduce<3>(
+                n,
+                [=] __device__(long long e, double *acc) {
+                    double2 wv = wj[e], zv = zj[e];
+                    for (int q = 0; q < j; ++q) {
+                        const double2 bq = ld2(beta + 2 * q);
+                        wv = csub(wv, cmul(bq, Lw.p[q][e]));
+                        zv = csub(zv, cmul(bq, Lz.p[q][e]));
+                    }
+                    wj[e] = wv;
+                    zj[e] = zv;
+                    acc_n2(acc, wv);
+                    acc_dot(acc + 1, wv, r[e]);
+                },
+                W, sc + S_NW, s, 2 * j + 5));
+            // normalise, then x += alpha z_j, r -= alpha w_j; ||r||^2
+            MGC_TRY(reduce<1>(
+                n,
+                [=] __device__(long long e, double *acc) {
+                    const double inv = 1.0 / sqrt(sc[S_NW]);
+                    const double2 alpha = make_double2(sc[S_WR] * inv, sc[S_WR + 1] * inv);
+                    double2 wv = wj[e], zv = zj[e];
+                    wv = make_double2(wv.x * inv, wv.y * inv);
+                    zv = make_double2(zv.x * inv, zv.y * inv);
+                    wj[e] = wv;
+                    zj[e] = zv;
+                    x[e] = cadd(x[e], cmul(alpha, zv));
+                    const double2 rv = csub(r[e], cmul(alpha, wv));
+                    r[e] = rv;
+                    acc_n2(acc, rv);
+                },
+                W, sc + S_RR, s, 8));
+            ++iters;
+            MGC_TRY(read_scalar(W, S_RR, &rr, s));
+            if (bad(rr)) {
+                info->iters = iters;
+                info->true_res = NAN;
+                return fail(MGC_ERR_BREAKDOWN, "FGCR: non-finite residual");
+            }
+            if (rr <= tol2) break;
+        }
+        // true residual
+        MGC_TRY(apply_D64(op, x, t, s));
+        MGC_TRY(residual(op, r, b, t, S_RR, s));
+        MGC_TRY(read_scalar(W, S_RR, &rr, s));
+        info->iters = iters;
+        info->true_res = std::sqrt(rr / bb);
+        if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "FGCR: non-finite true residual");
+        if (rr <= tol2) return MGC_OK;
+        if (iters >= p->max_iter) return MGC_NOT_CONVERGED;
+        info->restarts++;
+    }
+}
+
+// ------------------------------------------------------------------ flexible BiCGStab
+static int fbicgstab(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
+{
+    SolverWork *W = op->work;
+    const long long n = (long long)op->gauge->lat->g.V * 12;
+    double2 *x = W->x, *r = W->r, *b = W->b, *t = W->t;
+    double2 *r0 = W->w[0], *pv = W->w[1], *v = W->w[2], *sv = W->w[3];
+    double2 *ph = W->z[0], *sh = W->z[1];
+    double *sc = W->scal;
+    double bb, rr;
+    MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, b[e]); }, W, sc + S_BB, s, 1));
+    MGC_TRY(read_scalar(W, S_BB, &bb, s));
+    info->iters = 0;
+    info->restarts = 0;
+    if (bb == 0.0) {
+        MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+        info->true_res = 0;
+        return MGC_OK;
+    }
+    if (!p->x_is_guess) MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+    const double tol2 = p->tol * p->tol * bb;
+    int iters = 0;
+    for (;;) {
+        // r = b - D x, r0 = p = r, rho = <r0, r>
+        MGC_TRY(apply_D64(op, x, t, s));
+        MGC_TRY(reduce<2>(
+            n,
+            [=] __device__(long long e, double *acc) {
+                const double2 vv = csub(b[e], t[e]);
+                r[e] = vv;
+                r0[e] = vv;
+                pv[e] = vv;
+                acc_dot(acc, vv, vv);
+            },
+            W, sc + S_RHO, s, 5));
+        if (iters == 0 && p->x_is_guess) {
+            MGC_TRY(read_scalar(W, S_RHO, &rr, s));
+            info->true_res = std::sqrt(rr / bb);
+            if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "BiCGStab: non-finite initial residual");
+            if (rr <= tol2) return MGC_OK;
+        }
+        bool restart = false;
+        while (iters < p->max_iter) {
+            MGC_TRY(precondition(op, p, pv, ph, s));
+            MGC_TRY(apply_D64(op, ph, v, s));
+            MGC_TRY(reduce<2>(n, [=] __device__(long long e, double *acc) { acc_dot(acc, r0[e], v[e]); }, W, sc + S_R0V, s, 2));
+            // s = r - alpha v
+            MGC_TRY(map(
+                n,
+                [=] __device__(long long e) {
+                    const double2 alpha = cdiv(ld2(sc + S_RHO), ld2(sc + S_R0V));
+                    sv[e] = csub(r[e], cmul(alpha, v[e]));
+                },
+                s, 3));
+            MGC_TRY(precondition(op, p, sv, sh, s));
+            MGC_TRY(apply_D64(op, sh, t, s));
+            MGC_TRY(reduce<3>(
+                n,
+                [=] __device__(long long e, double *acc) {
+                    acc_dot(acc, t[e], sv[e]);
+                    acc_n2(acc + 2, t[e]);
+                },
+                W, sc + S_TS, s, 2));
+            // x += alpha ph + omega sh, r = s - omega t; ||r||^2 and <r0, r>
+            MGC_TRY(reduce<3>(
+                n,
+                [=] __device__(long long e, double *acc) {
+                    const double2 alpha = cdiv(ld2(sc + S_RHO), ld2(sc + S_R0V));
+                    const double tt = sc[S_TT];
+                    const double2 omega = tt > 0 ? make_double2(sc[S_TS] / tt, sc[S_TS + 1] / tt) : make_double2(0, 0);
+                    x[e] = cadd(x[e], cadd(cmul(alpha, ph[e]), cmul(omega, sh[e])));
+                    const double2 rv = csub(sv[e], cmul(omega, t[e]));
+                    r[e] = rv;
+                    acc_n2(acc, rv);
+                    acc_dot(acc + 1, r0[e], rv);
+                },
+                W, sc + S_RR, s, 8));
+            ++iters;
+            // slots S_RR, S_RR+1, S_RR+2 hold ||r||^2 and <r0, r>
+            double h[3];
+            MGC_CUDA(cudaMemcpyAsync(W->hscal, sc + S_RR, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            MGC_CUDA(cudaStreamSynchronize(s));
+            for (int k = 0; k < 3; ++k) h[k] = W->hscal[k];
+            rr = h[0];
+            if (bad(rr)) {
+                info->iters = iters;
+                info->true_res = NAN;
+                return fail(MGC_ERR_BREAKDOWN, "BiCGStab: non-finite residual");
+            }
+            if (rr <= tol2) break;
+            if (h[1] == 0.0 && h[2] == 0.0) { restart = true; break; }
+            // p = r + beta (p - omega v), beta = (rho1 / rho)(alpha / omega); rho = rho1
+            MGC_TRY(map(
+                n,
+                [=] __device__(long long e) {
+                    const double2 rho = ld2(sc + S_RHO);
+                    const double2 rho1 = ld2(sc + S_RR + 1);
+                    const double2 alpha = cdiv(rho, ld2(sc + S_R0V));
+                    const double tt = sc[S_TT];
+                    const double2 omega = make_double2(sc[S_TS] / tt, sc[S_TS + 1] / tt);
+                    const double2 beta = cmul(cdiv(rho1, rho), cdiv(alpha, omega));
+                    pv[e] = cadd(r[e], cmul(beta, csub(pv[e], cmul(omega, v[e]))));
+                },
+                s, 4));
+            MGC_CUDA(cudaMemcpyAsync(sc + S_RHO, sc + S_RR + 1, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        MGC_TRY(apply_D64(op, x, t, s));
+        MGC_TRY(residual(op, r, b, t, S_RR, s));
+        MGC_TRY(read_scalar(W, S_RR, &rr, s));
+        info->iters = iters;
+        info->true_res = std::sqrt(rr / bb);
+        if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "BiCGStab: non-finite true residual");
+        if (rr <= tol2) return MGC_OK;
+        if (iters >= p->max_iter) return MGC_NOT_CONVERGED;
+        (void)restart;
+        info->restarts++;
+    }
+}
+
+// ------------------------------------------------------------------ entry points
+static int check_params(const mgc_clover_s *op, const mgc_solve_params *p)
+{
+    if (p->method != 0 && p->method != 1) return fail(MGC_ERR_INVALID_ARG, "method must be 0 (FGCR) or 1 (BiCGStab)");
+    if (p->precond != 0 && p->precond != 1) return fail(MGC_ERR_INVALID_ARG, "precond must be 0 or 1");
+    if (p->precond == 1 && p->smoother_prec != 64 && p->smoother_prec != op->gauge->prec)
+        return fail(MGC_ERR_INVALID_ARG, "smoother_prec must be 64 or the gauge storage precision");
+    if (p->restart < 1 || p->restart > MAXM) return fail(MGC_ERR_INVALID_ARG, "restart must be in 1..32");
+    if (!(p->tol > 0) || p->max_iter < 1 || p->n_cy < 0 || p->n_mr < 0)
+        return fail(MGC_ERR_INVALID_ARG, "tol, max_iter, n_cy or n_mr out of range");
+    return MGC_OK;
+}
+
+int solve_packed(mgc_clover_s *op, const double2 *b, double2 *x, const mgc_solve_params *p, mgc_solve_info *info,
+                 cudaStream_t s)
+{
+    MGC_TRY(check_params(op, p));
+    MGC_TRY(ensure_work(op, p->restart, p->precond ? p->smoother_prec : 64));
+    SolverWork *W = op->work;
+    const size_t vb = spinor_bytes(op->gauge->lat->g, 64, 1);
+    MGC_CUDA(cudaMemcpyAsync(W->b, b, vb, cudaMemcpyDeviceToDevice, s));
+    if (p->x_is_guess) MGC_CUDA(cudaMemcpyAsync(W->x, x, vb, cudaMemcpyDeviceToDevice, s));
+    const int st = (p->method == 0) ? fgcr(op, p, info, s) : fbicgstab(op, p, info, s);
+    info->status = st;
+    MGC_CUDA(cudaMemcpyAsync(x, W->x, vb, cudaMemcpyDeviceToDevice, s));
+    return st;
+}
+
+int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solve_params *p, mgc_solve_info *info,
+          cudaStream_t s)
+{
+    MGC_TRY(check_params(op, p));
+    MGC_TRY(ensure_work(op, p->restart, p->precond ? p->smoother_prec : 64));
+    SolverWork *W = op->work;
+    const Geom &g = op->gauge->lat->g;
+    const size_t vb = spinor_bytes(g, 64, 1);
+    int worst = MGC_OK;
+    mgc_solve_info agg{MGC_OK, 0, 0, 0.0};
+    for (int k = 0; k < nrhs; ++k) {
+        const double *bk = b + (size_t)k * g.V * 24;
+        double *xk = x + (size_t)k * g.V * 24;
+        if (p->on_device) {
+            MGC_TRY(launch_pack(g, 64, 1, bk, W->b, s));
+            if (p->x_is_guess) MGC_TRY(launch_pack(g, 64, 1, xk, W->x, s));
+        } else {
+            MGC_CUDA(cudaMemcpyAsync(W->stage, bk, vb, cudaMemcpyHostToDevice, s));
+            MGC_TRY(launch_pack(g, 64, 1, (const double *)W->stage, W->b, s));
+            if (p->x_is_guess) {
+                MGC_CUDA(cudaMemcpyAsync(W->stage, xk, vb, cudaMemcpyHostToDevice, s));
+                MGC_TRY(launch_pack(g, 64, 1, (const double *)W->stage, W->x, s));
+            }
+        }
+        mgc_solve_info one{MGC_OK, 0, 0, 0.0};
+        const int st = (p->method == 0) ? fgcr(op, p, &one, s) : fbicgstab(op, p, &one, s);
+        if (st != MGC_OK && st != MGC_NOT_CONVERGED) {
+            one.status = st;
+            *info = one;
+            return st;
+        }
+        if (p->on_device) {
+            MGC_TRY(launch_unpack(g, 64, 1, W->x, xk, s));
+        } else {
+            MGC_TRY(launch_unpack(g, 64, 1, W->x, (double *)W->stage, s));
+            MGC_CUDA(cudaMemcpyAsync(xk, W->stage, vb, cudaMemcpyDeviceToHost, s));
+        }
+        if (st != MGC_OK) worst = st;
+        agg.iters = one.iters > agg.iters ? one.iters : agg.iters;
+        agg.restarts += one.restarts;
+        agg.true_res = one.true_res > agg.true_res ? one.true_res : agg.true_res;
+    }
+    MGC_CUDA(cudaStreamSynchronize(s));
+    agg.status = worst;
+    *info = agg;
+    return worst;
+}
+
+}  // namespace mgc

@@ -1,0 +1,108 @@
+"""The FP64 flexible outer solve (Sec. 3) with the SAP preconditioner in
+FP64, FP32 or FP16 storage: the true residual ||b - D x|| / ||b||, recomputed
+by the FP64 oracle, must be <= 1e-10.  Krylov iterates are not unique, so the
+solution is compared with the oracle's through the residual and, on small
+lattices, against the oracle's own solve."""
+import numpy as np
+import pytest
+
+from helpers import fields, rel
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _op(name, prec, compress=18):
+    from paper_2112_00501_gb300 import api
+
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    lat = api.Lattice(dims, block, -1)
+    g = api.Gauge(lat, torch.from_numpy(U).cuda(), storage_prec=prec, compress=compress)
+    return api.CloverOperator(g, kappa, csw)
+
+
+def _oracle_residual(name, x):
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    if np.prod(dims) <= 8 ** 4:
+        Dx = O.dirac(dims, -1, kappa, U, O.clover(dims, kappa, csw, U), x)
+    else:
+        Dx = O.dirac_at(dims, -1, kappa, csw, U, x, np.arange(np.prod(dims))).reshape(x.shape)
+    return float(np.linalg.norm(psi - Dx) / np.linalg.norm(psi))
+
+
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("smoother,compress", [(64, 18), (32, 18), (16, 12)])
+@pytest.mark.parametrize("name", ["c0_4^4", "mid_8^4"])
+def test_solve_reaches_1e10(name, method, smoother, compress):
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    op = _op(name, smoother if smoother != 64 else 32, compress)
+    x, info = op.solve(torch.from_numpy(psi).cuda(), method=method, smoother_prec=smoother, tol=1e-10)
+    assert info.status == 0
+    assert info.true_res <= 1e-10
+    xr = x.cpu().numpy()
+    assert _oracle_residual(name, xr) <= 1e-10
+    xo, st, it, res = O.solve(dims, block, -1, kappa, U, O.clover(dims, kappa, csw, U), psi, tol=1e-12)
+    assert rel(xr, xo) < 1e-8
+
+
+def test_unpreconditioned_and_host_pointer_paths():
+    name = "c0_4^4"
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    op = _op(name, 32)
+    x1, i1 = op.solve(torch.from_numpy(psi).cuda(), precond=0)
+    assert i1.status == 0 and _oracle_residual(name, x1.cpu().numpy()) <= 1e-10
+    x2, i2 = op.solve(psi, smoother_prec=32)  # host numpy source: host-pointer path
+    assert not x2.is_cuda and i2.status == 0
+    x3, i3 = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=32)
+    assert np.array_equal(x2.numpy(), x3.cpu().numpy())
+
+
+def test_multiple_rhs_and_initial_guess():
+    from paper_2112_00501_gb300 import synth
+
+    name = "mid_8^4"
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    op = _op(name, 16, 12)
+    bs = synth.gaussian_spinor(dims, 700, nrhs=2)
+    x, info = op.solve(torch.from_numpy(bs).cuda(), smoother_prec=16)
+    assert info.status == 0
+    for k in range(2):
+        Cl = O.clover(dims, kappa, csw, U)
+        r = bs[k] - O.dirac(dims, -1, kappa, U, Cl, x[k].cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(bs[k]) <= 1e-10
+    # starting from the solution costs no iterations
+    x2, info2 = op.solve(torch.from_numpy(bs[0]).cuda(), smoother_prec=16, x0=x[0])
+    assert info2.status == 0 and info2.iters == 0
+
+
+def test_solver_failure_modes_reported():
+    """Host-injected faults: a NaN source is a breakdown, a zero source gives
+    x = 0, and too few iterations give NOT_CONVERGED with the residual filled."""
+    from paper_2112_00501_gb300 import _lib
+
+    name = "c0_4^4"
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    op = _op(name, 32)
+    bad = psi.copy()
+    bad[3, 1, 2] = np.nan
+    with pytest.raises(_lib.MgcError) as e:
+        op.solve(torch.from_numpy(bad).cuda(), smoother_prec=32)
+    assert e.value.status == _lib.MGC_ERR_BREAKDOWN
+    x, info = op.solve(torch.zeros_like(torch.from_numpy(psi)).cuda(), smoother_prec=32)
+    assert info.status == 0 and float(x.abs().max()) == 0.0
+    x, info = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=32, max_iter=1, n_cy=1, n_mr=1)
+    assert info.status == _lib.MGC_NOT_CONVERGED and 0 < info.true_res < 1
+    with pytest.raises(_lib.MgcError) as e:
+        op.solve(torch.from_numpy(psi).cuda(), smoother_prec=16)  # gauge stored at FP32
+    assert e.value.status == _lib.MGC_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name,prec,compress", [("c1_16^3x32", 32, 18), ("c2_32^3x64", 16, 12)])
+def test_full_size_solve(name, prec, compress):
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    op = _op(name, prec, compress)
+    x, info = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=prec)
+    assert info.status == 0 and info.true_res <= 1e-10
+    assert _oracle_residual(name, x.cpu().numpy()) <= 1e-10
