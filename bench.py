@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Dslash/SAP sweep GB/s & %HBM peak; mixed vs FP64 time-to-1e-10 solve"
 WORKLOAD = dict(name="32^3x64", dims=(32, 32, 32, 64), block=(4, 4, 4, 4), eps=0.5, kappa=0.1370,
-                csw=1.0, config_index=2, prec=16, compress=12, n_cy=4, n_mr=4, restart=16, tol=1e-10)
+                csw=1.0, config_index=2, prec=16, compress=12, n_cy=4, n_mr=4, restart=16, tol=1e-10, inner_tol=2e-6)
 # bounded CPU sample of the same recipe (same eps, kappa, c_sw, solver) at 1/64 of the volume
 CPU_SAMPLE_DIMS = (16, 16, 16, 8)
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
@@ -41,8 +41,8 @@ FLOP_D = 1872.0
 def workload_desc(w):
     return (f"clover-Wilson {w['name']}, eps={w['eps']}, kappa={w['kappa']}, c_sw={w['csw']}, "
             f"FP16 storage + per-site FP32 scale, 12-real links, FP32 smoother arithmetic, "
-            f"SAP {w['n_cy']} sweeps x {w['n_mr']} MR on 4^4 domains, FGCR({w['restart']}) FP64 outer, "
-            f"tol {w['tol']:g}")
+            f"SAP {w['n_cy']} sweeps x {w['n_mr']} MR on 4^4 domains, FP32 FGCR({w['restart']}) inner solve "
+            f"to {w['inner_tol']:g} inside FP64 defect correction, tol {w['tol']:g}")
 
 
 def measured_peaks():
@@ -264,8 +264,8 @@ def main():
     gauge = api.Gauge(lat, Ud, storage_prec=w["prec"], compress=w["compress"])
     op = api.CloverOperator(gauge, w["kappa"], w["csw"])
     b = torch.from_numpy(b_host).cuda()
-    params = api.solve_params(method=0, precond=1, smoother_prec=w["prec"], n_cy=w["n_cy"], n_mr=w["n_mr"],
-                              restart=w["restart"], tol=w["tol"], max_iter=500)
+    params = api.solve_params(method=2, precond=1, smoother_prec=w["prec"], n_cy=w["n_cy"], n_mr=w["n_mr"],
+                              restart=w["restart"], tol=w["tol"], max_iter=500, inner_tol=w["inner_tol"])
     stream = torch.cuda.current_stream()
 
     def barrier():

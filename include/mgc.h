@@ -119,8 +119,9 @@ int mgc_spinor_convert(mgc_lattice_t lat, int nrhs, int prec_in, const void *in,
 /*
  * Gauge field U (canonical complex128, V*4*9 entries; host memory if
  * on_device == 0, else device memory).  The handle keeps an FP64 copy for the
- * outer solver and a copy at storage_prec (32 or 16; 64 adds nothing) with
- * compress = 18 (full matrices) or 12 (rows 0 and 1; row 2 is rebuilt as
+ * outer solver, an FP32 copy when storage_prec <= 32 (inner Krylov operator)
+ * and an FP16 copy when storage_prec == 16 (smoother); the low-precision
+ * copies use compress = 18 (full matrices) or 12 (rows 0 and 1; row 2 is rebuilt as
  * conj(row0 x row1), which needs SU(3) links: with compress = 12 the call
  * returns MGC_ERR_NOT_UNITARY when any link's unitarity or determinant error
  * exceeds 1e-10).  Synchronises stream.
@@ -132,18 +133,34 @@ int mgc_gauge_destroy(mgc_gauge_t g);
 /*
  * The clover-Wilson operator D = C - kappa*H (Eq. (1)).  C and C^-1 are
  * computed on the GPU in FP64 from the gauge field's clover leaves (Sec. 2:
- * computing C and C^-1 from the gauge field); a copy of C at the gauge's
- * storage precision is kept for the smoother.  The gauge handle must outlive
+ * computing C and C^-1 from the gauge field); copies of C at FP32 and FP16
+ * follow the gauge field's copies.  The gauge handle must outlive
  * the operator.  Synchronises stream.
  */
 int mgc_clover_create(mgc_gauge_t g, double kappa, double csw, void *stream, mgc_clover_t *out);
 int mgc_clover_destroy(mgc_clover_t op);
+/*
+ * The operator's device status word (no paper counterpart): kernels that wait
+ * on their own asynchronous copies give up after a bounded time and set a bit
+ * here instead of hanging.  *flags receives the word; clear != 0 zeroes it.
+ * Returns MGC_ERR_TIMEOUT when any bit is set.  Synchronises stream.
+ * mgc_solve and mgc_force check it themselves.
+ */
+int mgc_device_status(mgc_clover_t op, int *flags, int clear, void *stream);
+/*
+ * Self-test of that bounded-wait mechanism (no paper counterpart): one thread
+ * block waits on a shared-memory barrier for at most limit_ns (<= 2 s).  With
+ * arrive != 0 the barrier completes and the call returns MGC_OK; with
+ * arrive == 0 nothing arrives, the wait runs out, *flag_out is non-zero and the
+ * call returns MGC_ERR_TIMEOUT with the context still usable.
+ */
+int mgc_selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, void *stream);
 /* C (inverse = 0) or C^-1 (inverse = 1) as canonical 12x12 complex128 per site (device). */
 int mgc_clover_export(mgc_clover_t op, int inverse, double *out, void *stream);
 
 /*
  * out = D in and out = D^dagger in (= gamma5 D gamma5 in) for nrhs packed
- * spinors at precision prec (64, or the gauge's storage_prec).  Eq. (1).
+ * spinors at precision prec (64, or 32/16 when the gauge keeps that copy).  Eq. (1).
  * in and out must not overlap.  Asynchronous on stream.
  */
 int mgc_apply_D(mgc_clover_t op, const void *in, void *out, int nrhs, int prec, void *stream);
@@ -168,24 +185,34 @@ int mgc_apply_clover(mgc_clover_t op, const void *in, void *out, int nrhs, int p
 int mgc_sap_smooth(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, int n_mr,
                    int prec, int x_is_zero, void *stream);
 
-/* outer solver parameters (Sec. 3: flexible outer solver, SAP preconditioner) */
+/*
+ * Solver parameters (Sec. 3: flexible outer solver with the SAP smoother as
+ * preconditioner; Sec. 2: QWS's double-precision Richardson iteration around a
+ * single-precision solver).  Methods:
+ *   0  FGCR(restart) with FP64 Krylov vectors, FP64 D in every iteration;
+ *   1  flexible BiCGStab (the paper's outer solver) with FP64 vectors;
+ *   2  two-level: FP64 defect correction (residual b - D x, D and x in FP64)
+ *      around an FP32 FGCR(restart) + SAP inner solve to inner_tol, whose
+ *      inner products accumulate in FP64 across the lattice.
+ */
 typedef struct {
-    int method;        /* 0 = FGCR(restart), 1 = flexible BiCGStab */
+    int method;        /* 0, 1 or 2 (above) */
     int precond;       /* 0 = none, 1 = SAP */
-    int smoother_prec; /* 64, 32 or 16 (16/32 need the gauge's storage_prec) */
+    int smoother_prec; /* 64, 32 or 16 (needs a copy at that precision; 32/16 for method 2) */
     int n_cy;          /* SAP sweeps per preconditioner application */
     int n_mr;          /* MR steps per domain */
-    int restart;       /* FGCR restart length m (<= 32) */
+    int restart;       /* FGCR length m (<= 32); method 2: inner iterations per pass */
     double tol;        /* stop when ||b - D x|| <= tol ||b||, D in FP64 */
-    int max_iter;      /* outer iterations (preconditioner applications for FGCR) */
+    int max_iter;      /* preconditioner applications (methods 0, 2), BiCGStab iterations (1) */
     int on_device;     /* 1: b, x are device pointers; 0: host pointers */
     int x_is_guess;    /* 1: x holds the initial guess; 0: start from x = 0 */
+    double inner_tol;  /* method 2: relative residual reduction of each inner solve */
 } mgc_solve_params;
 
 typedef struct {
     int status;        /* MGC_OK, MGC_NOT_CONVERGED or MGC_ERR_BREAKDOWN */
-    int iters;         /* outer iterations taken (max over right-hand sides) */
-    int restarts;      /* true-residual recomputations */
+    int iters;         /* preconditioned iterations (max over right-hand sides) */
+    int restarts;      /* true-residual recomputations (method 2: outer passes) */
     double true_res;   /* max over rhs of ||b - D x|| / ||b|| in FP64 */
 } mgc_solve_info;
 

@@ -34,6 +34,7 @@ class SolveParams(C.Structure):
         ("max_iter", C.c_int),
         ("on_device", C.c_int),
         ("x_is_guess", C.c_int),
+        ("inner_tol", C.c_double),
     ]
 
 
@@ -66,6 +67,8 @@ SIGNATURES = {
     "mgc_gauge_destroy": (_I, [_P]),
     "mgc_clover_create": (_I, [_P, _D, _D, _P, C.POINTER(_P)]),
     "mgc_clover_destroy": (_I, [_P]),
+    "mgc_device_status": (_I, [_P, C.POINTER(_I), _I, _P]),
+    "mgc_selftest_bounded_wait": (_I, [C.c_longlong, _I, C.POINTER(_I), _P]),
     "mgc_clover_export": (_I, [_P, _I, _P, _P]),
     "mgc_apply_D": (_I, [_P, _P, _P, _I, _I, _P]),
     "mgc_apply_Ddag": (_I, [_P, _P, _P, _I, _I, _P]),

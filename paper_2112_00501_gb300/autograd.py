@@ -16,7 +16,10 @@ from .api import CloverOperator, Gauge, Lattice, solve_params
 class FermionAction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, U, phi, lattice: Lattice, kappa: float, csw: float, params):
-        gauge = Gauge(lattice, U.detach(), storage_prec=params.smoother_prec if params.precond else 64)
+        prec = params.smoother_prec if params.precond else 64
+        if params.method == 2:
+            prec = min(prec, 32)
+        gauge = Gauge(lattice, U.detach(), storage_prec=prec)
         op = CloverOperator(gauge, kappa, csw)
         g, S, info = op.force(phi.detach(), params)
         ctx.save_for_backward(g)

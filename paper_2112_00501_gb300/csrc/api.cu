@@ -23,10 +23,25 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line)
     char buf[512];
     snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
     g_last_error = buf;
+    // clear the runtime's last-error state so that a later launch check does
+    // not report this (non-sticky) error again
+    (void)cudaGetLastError();
     return MGC_ERR_CUDA;
 }
 
 int ok() { return MGC_OK; }
+
+int check_device_status(const mgc_clover_s *op, cudaStream_t s)
+{
+    int h = 0;
+    MGC_CUDA(cudaMemcpyAsync(&h, op->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MGC_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        MGC_CUDA(cudaMemsetAsync(op->d_status, 0, sizeof(int), s));
+        return fail(MGC_ERR_TIMEOUT, "a bounded device wait in the smoother ran out");
+    }
+    return MGC_OK;
+}
 
 static std::atomic<long long> g_launches{0};
 static std::atomic<long long> g_bytes{0};
@@ -181,7 +196,8 @@ int mgc_gauge_create(mgc_lattice_t lat, const double *U, int on_device, int stor
         cudaFree(d_err);
         if (code != MGC_OK) {
             cudaFree(G->U64);
-            cudaFree(G->Ulo);
+            cudaFree(G->U32);
+            cudaFree(G->U16);
             delete G;
         }
         return code;
@@ -210,9 +226,14 @@ int mgc_gauge_create(mgc_lattice_t lat, const double *U, int on_device, int stor
     GCUDA(cudaMalloc(&G->U64, gauge_bytes(g, 64, 18)));
     st = launch_gauge_pack(g, src, 64, 18, G->U64, s);
     if (st) return bail(st);
-    if (storage_prec != 64) {
-        GCUDA(cudaMalloc(&G->Ulo, gauge_bytes(g, storage_prec, G->compress)));
-        st = launch_gauge_pack(g, src, storage_prec, G->compress, G->Ulo, s);
+    if (storage_prec <= 32) {
+        GCUDA(cudaMalloc(&G->U32, gauge_bytes(g, 32, G->compress)));
+        st = launch_gauge_pack(g, src, 32, G->compress, G->U32, s);
+        if (st) return bail(st);
+    }
+    if (storage_prec == 16) {
+        GCUDA(cudaMalloc(&G->U16, gauge_bytes(g, 16, G->compress)));
+        st = launch_gauge_pack(g, src, 16, G->compress, G->U16, s);
         if (st) return bail(st);
     }
     GCUDA(cudaStreamSynchronize(s));
@@ -225,7 +246,8 @@ int mgc_gauge_destroy(mgc_gauge_t g)
 {
     if (!g) return MGC_OK;
     cudaFree(g->U64);
-    cudaFree(g->Ulo);
+    cudaFree(g->U32);
+    cudaFree(g->U16);
     delete g;
     return MGC_OK;
 }
@@ -245,7 +267,9 @@ int mgc_clover_create(mgc_gauge_t g, double kappa, double csw, void *stream, mgc
         if (code != MGC_OK) {
             cudaFree(op->C64);
             cudaFree(op->Ci64);
-            cudaFree(op->Clo);
+            cudaFree(op->C32);
+            cudaFree(op->C16);
+            cudaFree(op->d_status);
             delete op;
         }
         return code;
@@ -255,16 +279,23 @@ int mgc_clover_create(mgc_gauge_t g, double kappa, double csw, void *stream, mgc
         cudaError_t e_ = (call);                                                      \
         if (e_ != cudaSuccess) return bail(cuda_fail(e_, #call, __FILE__, __LINE__)); \
     } while (0)
+    CCUDA(cudaMalloc(&op->d_status, sizeof(int)));
+    CCUDA(cudaMemsetAsync(op->d_status, 0, sizeof(int), s));
     CCUDA(cudaMalloc(&op->C64, clover_bytes(geo, 64)));
     CCUDA(cudaMalloc(&op->Ci64, clover_bytes(geo, 64)));
     CCUDA(cudaMalloc(&d_bad, sizeof(int)));
     CCUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
     int st = launch_clover_build(geo, g->U64, kappa, csw, op->C64, op->Ci64, d_bad, s);
     if (st) return bail(st);
-    if (g->prec != 64) {
-        CCUDA(cudaMalloc(&op->Clo, clover_bytes(geo, g->prec)));
-        if (g->prec == 16) op->Clo_sc = (float *)((uint4 *)op->Clo + (size_t)geo.V * 9);
-        st = launch_clover_lowprec(geo, op->C64, g->prec, op->Clo, s);
+    if (g->prec <= 32) {
+        CCUDA(cudaMalloc(&op->C32, clover_bytes(geo, 32)));
+        st = launch_clover_lowprec(geo, op->C64, 32, op->C32, s);
+        if (st) return bail(st);
+    }
+    if (g->prec == 16) {
+        CCUDA(cudaMalloc(&op->C16, clover_bytes(geo, 16)));
+        op->C16_sc = (float *)((uint4 *)op->C16 + (size_t)geo.V * 9);
+        st = launch_clover_lowprec(geo, op->C64, 16, op->C16, s);
         if (st) return bail(st);
     }
     int bad = 0;
@@ -282,9 +313,27 @@ int mgc_clover_destroy(mgc_clover_t op)
     free_work(op);
     cudaFree(op->C64);
     cudaFree(op->Ci64);
-    cudaFree(op->Clo);
+    cudaFree(op->C32);
+    cudaFree(op->C16);
+    cudaFree(op->d_status);
     delete op;
     return MGC_OK;
+}
+
+int mgc_selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, void *stream)
+{
+    if (!flag_out || limit_ns <= 0 || limit_ns > 2000000000LL) return fail(MGC_ERR_INVALID_ARG, "bad argument");
+    return selftest_bounded_wait(limit_ns, arrive, flag_out, (cudaStream_t)stream);
+}
+
+int mgc_device_status(mgc_clover_t op, int *flags, int clear, void *stream)
+{
+    if (!op || !flags) return fail(MGC_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    MGC_CUDA(cudaMemcpyAsync(flags, op->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MGC_CUDA(cudaStreamSynchronize(s));
+    if (clear) MGC_CUDA(cudaMemsetAsync(op->d_status, 0, sizeof(int), s));
+    return *flags ? fail(MGC_ERR_TIMEOUT, "a bounded device wait ran out") : MGC_OK;
 }
 
 int mgc_clover_export(mgc_clover_t op, int inverse, double *out, void *stream)
@@ -329,7 +378,7 @@ int mgc_sap_smooth(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, 
 void mgc_solve_params_default(mgc_solve_params *p)
 {
     if (!p) return;
-    p->method = 0;
+    p->method = 2;
     p->precond = 1;
     p->smoother_prec = 32;
     p->n_cy = 4;
@@ -339,6 +388,7 @@ void mgc_solve_params_default(mgc_solve_params *p)
     p->max_iter = 500;
     p->on_device = 1;
     p->x_is_guess = 0;
+    p->inner_tol = 2e-6;
 }
 
 int mgc_solve(mgc_clover_t op, const double *b, double *x, int nrhs, const mgc_solve_params *p, mgc_solve_info *info,

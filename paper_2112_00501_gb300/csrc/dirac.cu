@@ -212,32 +212,31 @@ static void dirac_dispatch(const Geom &g, bool dag, SP in, SP out, GA U, CL C, d
 
 static Clover16 cl16(const Geom &g, const mgc_clover_s *op)
 {
-    return Clover16{(uint4 *)op->Clo, op->Clo_sc, g.lvb};
+    return Clover16{(uint4 *)op->C16, op->C16_sc, g.lvb};
 }
 
 int launch_dirac(const mgc_clover_s *op, int prec, bool dag, const void *in, void *out, int nrhs, cudaStream_t s)
 {
     const mgc_gauge_s *ga = op->gauge;
     const Geom &g = ga->lat->g;
+    if (!has_prec(ga, prec)) return fail(MGC_ERR_INVALID_ARG, "no copy of the operator at this precision");
     if (prec == 64) {
         dirac_dispatch(g, dag, sp64(g, in), sp64(g, out), Gauge64{ga->U64, g.lvb}, Clover64{op->C64, g.lvb},
                        op->kappa, nrhs, s);
-    } else if (prec != ga->prec) {
-        return fail(MGC_ERR_INVALID_ARG, "operator precision differs from the gauge storage precision");
     } else if (prec == 32) {
-        Clover32 C{(float4 *)op->Clo, g.lvb};
+        Clover32 C{(float4 *)op->C32, g.lvb};
         if (ga->compress == 12)
-            dirac_dispatch(g, dag, sp32(g, in), sp32(g, out), Gauge32x12{(float4 *)ga->Ulo, g.lvb}, C, op->kappa,
+            dirac_dispatch(g, dag, sp32(g, in), sp32(g, out), Gauge32x12{(float4 *)ga->U32, g.lvb}, C, op->kappa,
                            nrhs, s);
         else
-            dirac_dispatch(g, dag, sp32(g, in), sp32(g, out), Gauge32x18{(float2 *)ga->Ulo, g.lvb}, C, op->kappa,
+            dirac_dispatch(g, dag, sp32(g, in), sp32(g, out), Gauge32x18{(float2 *)ga->U32, g.lvb}, C, op->kappa,
                            nrhs, s);
     } else {
         if (ga->compress == 12)
-            dirac_dispatch(g, dag, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x12{(uint2 *)ga->Ulo, g.lvb},
+            dirac_dispatch(g, dag, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x12{(uint2 *)ga->U16, g.lvb},
                            cl16(g, op), op->kappa, nrhs, s);
         else
-            dirac_dispatch(g, dag, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x18{(uint32_t *)ga->Ulo, g.lvb},
+            dirac_dispatch(g, dag, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x18{(uint32_t *)ga->U16, g.lvb},
                            cl16(g, op), op->kappa, nrhs, s);
     }
     MGC_CUDA(cudaGetLastError());
@@ -272,15 +271,60 @@ int launch_clover_apply(const mgc_clover_s *op, int prec, bool inverse, const vo
                                             Clover64{inverse ? op->Ci64 : op->C64, g.lvb});
     } else if (inverse) {
         return fail(MGC_ERR_INVALID_ARG, "C^-1 is kept in FP64 only");
-    } else if (prec != op->gauge->prec) {
-        return fail(MGC_ERR_INVALID_ARG, "clover precision differs from the gauge storage precision");
+    } else if (!has_prec(op->gauge, prec)) {
+        return fail(MGC_ERR_INVALID_ARG, "no copy of the clover term at this precision");
     } else if (prec == 32) {
-        k_clover_apply<<<grid, 256, 0, s>>>(g, sp32(g, in), sp32(g, out), Clover32{(float4 *)op->Clo, g.lvb});
+        k_clover_apply<<<grid, 256, 0, s>>>(g, sp32(g, in), sp32(g, out), Clover32{(float4 *)op->C32, g.lvb});
     } else {
         k_clover_apply<<<grid, 256, 0, s>>>(g, sp16(g, in, nrhs), sp16(g, out, nrhs), cl16(g, op));
     }
     MGC_CUDA(cudaGetLastError());
     count(1, (double)g.V * (2.0 * nrhs * spinor_site_bytes(prec) + clover_site_bytes(prec)));
+    return MGC_OK;
+}
+
+// ------------------------------------------------------------------ mixed-precision site kernels
+// out32 = s * in64 (rounded to nearest) and x64 += c * e32, site by site so
+// that the two packed layouts line up component by component
+__global__ void k_scale_to32(Geom g, Spinor64 in, Spinor32 out, double s)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    Cx<double> v[12];
+    Cx<float> w[12];
+    in.load(i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = Cx<float>{(float)(s * v[k].r), (float)(s * v[k].i)};
+    out.store(i, w);
+}
+
+__global__ void k_axpy_from32(Geom g, Spinor64 x, Spinor32 e, double cr, double ci)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    Cx<double> v[12];
+    Cx<float> d[12];
+    x.load(i, v);
+    e.load(i, d);
+    const Cx<double> c = {cr, ci};
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = cfma(c, Cx<double>{(double)d[k].r, (double)d[k].i}, v[k]);
+    x.store(i, v);
+}
+
+int launch_scale_to32(const Geom &g, const double2 *in, void *out, double s, cudaStream_t st)
+{
+    k_scale_to32<<<grid_for(g.V, 256), 256, 0, st>>>(g, sp64(g, in), sp32(g, out), s);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * (192.0 + 96.0));
+    return MGC_OK;
+}
+
+int launch_axpy_from32(const Geom &g, double2 *x, const void *e, double cr, double ci, cudaStream_t st)
+{
+    k_axpy_from32<<<grid_for(g.V, 256), 256, 0, st>>>(g, sp64(g, x), sp32(g, e), cr, ci);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * (2 * 192.0 + 96.0));
     return MGC_OK;
 }
 

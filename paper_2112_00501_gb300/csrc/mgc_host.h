@@ -15,12 +15,16 @@ struct mgc_lattice_s {
     int block[4];
 };
 
+// A gauge field keeps an FP64 copy (outer solver, force, clover build) and one
+// copy at every precision from FP32 down to its storage precision: FP32 for the
+// inner Krylov operator of the two-level solve, FP16 for the smoother.
 struct mgc_gauge_s {
     mgc_lattice_s *lat;
     double2 *U64;  // packed FP64, 18 reals per link
-    void *Ulo;     // packed copy at prec/compress (NULL when prec == 64)
-    int prec;      // 64, 32 or 16
-    int compress;  // 18 or 12
+    void *U32;     // packed FP32 at compress (NULL when prec == 64)
+    void *U16;     // packed FP16 at compress (NULL unless prec == 16)
+    int prec;      // storage precision: 64, 32 or 16
+    int compress;  // 18 or 12 for the FP32/FP16 copies
 };
 
 namespace mgc {
@@ -32,10 +36,24 @@ struct mgc_clover_s {
     double kappa, csw;
     double2 *C64;   // packed FP64 clover C
     double2 *Ci64;  // packed FP64 C^-1
-    void *Clo;      // packed C at gauge->prec (NULL when prec == 64)
-    float *Clo_sc;  // per-site scales of the FP16 clover
+    void *C32;      // packed FP32 C (NULL when prec == 64)
+    void *C16;      // packed FP16 C followed by its per-site scales (prec == 16)
+    float *C16_sc;
+    int *d_status;  // device status word: bits set by kernels whose bounded waits ran out
     mgc::SolverWork *work;
 };
+
+namespace mgc {
+// MGC_ERR_TIMEOUT if a kernel of this operator recorded a timed-out wait
+// (reads and clears the device status word; synchronises the stream)
+int check_device_status(const mgc_clover_s *op, cudaStream_t s);
+}
+
+// true when the operator holds a copy of its fields at precision prec
+inline bool has_prec(const mgc_gauge_s *g, int prec)
+{
+    return prec == 64 || (prec == 32 && g->prec <= 32) || (prec == 16 && g->prec == 16);
+}
 
 namespace mgc {
 
@@ -81,6 +99,9 @@ int launch_dirac(const mgc_clover_s *op, int prec, bool dag, const void *in, voi
 int launch_clover_apply(const mgc_clover_s *op, int prec, bool inverse, const void *in, void *out, int nrhs,
                         cudaStream_t s);
 int launch_gamma5(const Geom &g, int nrhs, const double2 *in, double2 *out, cudaStream_t s);
+// out (packed FP32) = s * in (packed FP64); x (packed FP64) += (cr + i ci) * e (packed FP32)
+int launch_scale_to32(const Geom &g, const double2 *in, void *out, double s, cudaStream_t st);
+int launch_axpy_from32(const Geom &g, double2 *x, const void *e, double cr, double ci, cudaStream_t st);
 
 // clover_build.cu
 int launch_clover_build(const Geom &g, const double2 *U64, double kappa, double csw, double2 *C64, double2 *Ci64,
@@ -92,6 +113,7 @@ int launch_unitarity(const Geom &g, const double *canon_dev, double *d_maxerr, c
 // sap.cu
 int launch_sap(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_mr,
                int x_is_zero, cudaStream_t s);
+int selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, cudaStream_t s);
 
 // solver.cu
 int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solve_params *p, mgc_solve_info *info,

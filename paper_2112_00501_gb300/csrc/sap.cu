@@ -13,6 +13,7 @@
 // are red then black and every block of a launch is independent.
 #include "hop.cuh"
 #include "mgc_host.h"
+#include "tma.cuh"
 
 namespace mgc {
 
@@ -184,6 +185,373 @@ static double sap_launch_bytes(const Geom &g, int prec, int compress, int nrhs, 
                         clover_site_bytes(prec));
 }
 
+// ------------------------------------------------------------------ staged kernel
+// The FP32/FP16-storage smoother keeps one domain's links and clover term in
+// shared memory for the whole domain solve.  In the packed layout they are
+// contiguous per domain, so one thread issues 1-D TMA bulk copies for them
+// (completed on an mbarrier) while the block computes the hopping part of the
+// domain residual from global memory.  r and e of the MR iteration also live in
+// shared memory, which keeps the kernel at two resident blocks per SM.
+
+// shared-memory views of one domain's links: the global plane layout with the
+// domain index dropped (site index l inside the domain)
+template <class GA> struct Staged;
+template <> struct Staged<Gauge16x12> {
+    static constexpr int BYTES = 96;  // per site, four links
+    const uint2 *s;
+    int lvb;
+    static __device__ const void *src(const Gauge16x12 &U, int blk) { return U.p + ((size_t)blk * 12 << U.lvb); }
+    __device__ __forceinline__ void load(int l, int mu, Cx<float> u[9]) const
+    {
+        const uint2 *q = s + ((mu * 3) << lvb) + l;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint2 v = q[k << lvb];
+            const float2 a = unpack_half2(v.x), b = unpack_half2(v.y);
+            u[2 * k] = {a.x, a.y};
+            u[2 * k + 1] = {b.x, b.y};
+        }
+        reconstruct_row2(u);
+    }
+};
+template <> struct Staged<Gauge16x18> {
+    static constexpr int BYTES = 144;
+    const uint32_t *s;
+    int lvb;
+    static __device__ const void *src(const Gauge16x18 &U, int blk) { return U.p + ((size_t)blk * 36 << U.lvb); }
+    __device__ __forceinline__ void load(int l, int mu, Cx<float> u[9]) const
+    {
+        const uint32_t *q = s + ((mu * 9) << lvb) + l;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float2 a = unpack_half2(q[k << lvb]);
+            u[k] = {a.x, a.y};
+        }
+    }
+};
+template <> struct Staged<Gauge32x12> {
+    static constexpr int BYTES = 192;
+    const float4 *s;
+    int lvb;
+    static __device__ const void *src(const Gauge32x12 &U, int blk) { return U.p + ((size_t)blk * 12 << U.lvb); }
+    __device__ __forceinline__ void load(int l, int mu, Cx<float> u[9]) const
+    {
+        const float4 *q = s + ((mu * 3) << lvb) + l;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 v = q[k << lvb];
+            u[2 * k] = {v.x, v.y};
+            u[2 * k + 1] = {v.z, v.w};
+        }
+        reconstruct_row2(u);
+    }
+};
+template <> struct Staged<Gauge32x18> {
+    static constexpr int BYTES = 288;
+    const float2 *s;
+    int lvb;
+    static __device__ const void *src(const Gauge32x18 &U, int blk) { return U.p + ((size_t)blk * 36 << U.lvb); }
+    __device__ __forceinline__ void load(int l, int mu, Cx<float> u[9]) const
+    {
+        const float2 *q = s + ((mu * 9) << lvb) + l;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float2 v = q[k << lvb];
+            u[k] = {v.x, v.y};
+        }
+    }
+};
+
+// the clover term of one domain in shared memory; mul() applies it to a site
+template <class CL> struct StagedC;
+template <> struct StagedC<Clover16> {
+    static constexpr int BYTES = 144, SCALE = 4;
+    const uint4 *s;
+    const float *sc;
+    int lvb;
+    static __device__ const void *src(const Clover16 &C, int blk) { return C.p + ((size_t)blk * 9 << C.lvb); }
+    static __device__ const void *src_scale(const Clover16 &C, int blk) { return C.sc + ((size_t)blk << C.lvb); }
+    // the 72 halves pair up as (diagonal, diagonal) and (re, im) of the
+    // off-diagonal entries: 18 packed words per chiral block
+    __device__ __forceinline__ void mul(int l, const Cx<float> in[12], Cx<float> out[12]) const
+    {
+        uint32_t w[36];
+        const uint4 *q = s + l;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const uint4 v = q[k << lvb];
+            w[4 * k] = v.x;
+            w[4 * k + 1] = v.y;
+            w[4 * k + 2] = v.z;
+            w[4 * k + 3] = v.w;
+        }
+        const float scale = sc[l];
+#pragma unroll
+        for (int chi = 0; chi < 2; ++chi) {
+            const uint32_t *b = w + 18 * chi;
+            const Cx<float> *v = in + 6 * chi;
+            Cx<float> *o = out + 6 * chi;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float2 d = unpack_half2(b[a]);
+                o[2 * a] = d.x * v[2 * a];
+                o[2 * a + 1] = d.y * v[2 * a + 1];
+            }
+            int k = 3;
+#pragma unroll
+            for (int a = 1; a < 6; ++a)
+#pragma unroll
+                for (int c = 0; c < a; ++c) {
+                    const float2 L = unpack_half2(b[k++]);
+                    const Cx<float> Lc = {L.x, L.y};
+                    o[a] = cfma(Lc, v[c], o[a]);
+                    o[c] = cjfma(Lc, v[a], o[c]);
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[k] = scale * out[k];
+    }
+};
+template <> struct StagedC<Clover32> {
+    static constexpr int BYTES = 288, SCALE = 0;
+    const float4 *s;
+    const float *sc;
+    int lvb;
+    static __device__ const void *src(const Clover32 &C, int blk) { return C.p + ((size_t)blk * 18 << C.lvb); }
+    static __device__ const void *src_scale(const Clover32 &, int) { return nullptr; }
+    __device__ __forceinline__ void mul(int l, const Cx<float> in[12], Cx<float> out[12]) const
+    {
+        float c[72];
+        const float4 *q = s + l;
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {
+            const float4 v = q[k << lvb];
+            c[4 * k] = v.x;
+            c[4 * k + 1] = v.y;
+            c[4 * k + 2] = v.z;
+            c[4 * k + 3] = v.w;
+        }
+        clover_mul(c, in, out);
+    }
+};
+
+template <int MU, class SL>
+__device__ __forceinline__ void staged_hop_dir(const SL &U, int l, int nf, int nb, const Cx<float> *rs, int vb,
+                                               Cx<float> acc[12])
+{
+    Cx<float> s[12], h[6], w[6], u[9];
+    if (nf >= 0) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s[k] = rs[k * vb + nf];
+        project<MU, -1>(s, h);
+        U.load(l, MU, u);
+        su3_mul(u, h, w);
+        reconstruct_add<MU, -1>(acc, w);
+    }
+    if (nb >= 0) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s[k] = rs[k * vb + nb];
+        project<MU, +1>(s, h);
+        U.load(nb, MU, u);
+        su3_dag_mul(u, h, w);
+        reconstruct_add<MU, +1>(acc, w);
+    }
+}
+
+// shared-memory bytes of the staged kernel for a domain of vb sites
+template <class GA, class CL>
+static size_t staged_smem(int vb)
+{
+    return (size_t)vb * (Staged<GA>::BYTES + StagedC<CL>::BYTES + StagedC<CL>::SCALE + 2 * 12 * sizeof(Cx<float>)) +
+           96 * sizeof(float) + 16;
+}
+
+template <class SP, class GA, class CL>
+__global__ void __launch_bounds__(256, 2) k_sap_staged(Geom g, SP b, SP x, GA U, CL C, float kappa, int colour,
+                                                       int nmr, int x_zero, int *status)
+{
+    using SL = Staged<GA>;
+    using SC = StagedC<CL>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int vb = 1 << g.lvb;
+    unsigned char *sp = smem;
+    void *s_links = sp;
+    sp += (size_t)SL::BYTES * vb;
+    void *s_clov = sp;
+    sp += (size_t)SC::BYTES * vb;
+    float *s_scale = reinterpret_cast<float *>(sp);
+    sp += (size_t)SC::SCALE * vb;
+    Cx<float> *rs = reinterpret_cast<Cx<float> *>(sp);
+    sp += (size_t)12 * vb * sizeof(Cx<float>);
+    Cx<float> *es = reinterpret_cast<Cx<float> *>(sp);
+    sp += (size_t)12 * vb * sizeof(Cx<float>);
+    float *red = reinterpret_cast<float *>(sp);
+    sp += 96 * sizeof(float);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sp);
+
+    const int rr = blockIdx.y;
+    const SP bb = shift_rhs(b, rr, g.V);
+    const SP xx = shift_rhs(x, rr, g.V);
+    int j = blockIdx.x;
+    const int half0 = g.NB[0] >> 1;
+    int bc[4];
+    const int m = j % half0;
+    j /= half0;
+    bc[1] = j % g.NB[1];
+    j /= g.NB[1];
+    bc[2] = j % g.NB[2];
+    bc[3] = j / g.NB[2];
+    bc[0] = 2 * m + ((colour + bc[1] + bc[2] + bc[3]) & 1);
+    const int blk = block_index(g, bc);
+    const int l = threadIdx.x;
+    const int i = (blk << g.lvb) | l;
+
+    // stage the domain's links and clover term
+    if (l == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (l == 0) {
+        const unsigned lb = SL::BYTES * vb, cb = SC::BYTES * vb, sb = SC::SCALE * vb;
+        mbar_arrive_expect_tx(bar, lb + cb + sb);
+        bulk_g2s(s_links, SL::src(U, blk), lb, bar);
+        bulk_g2s(s_clov, SC::src(C, blk), cb, bar);
+        if (SC::SCALE) bulk_g2s(s_scale, SC::src_scale(C, blk), sb, bar);
+    }
+    const SL Us{reinterpret_cast<decltype(SL::s)>(s_links), g.lvb};
+    const SC Cs{reinterpret_cast<decltype(SC::s)>(s_clov), s_scale, g.lvb};
+
+    int lc[4], c[4];
+    local_coords(g, l, lc);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) c[mu] = (bc[mu] << g.lb[mu]) + lc[mu];
+
+    // 1. the hopping part of D x from global memory while the copies land
+    Cx<float> acc[12], xs[12];
+    if (!x_zero) hop_site<false>(g, c, i, xx, U, acc);
+
+    const bool ok = mbar_wait_bounded(bar, 0, WAIT_LIMIT_NS);
+    if (!__syncthreads_and(ok)) {
+        // give the copies in flight a second bounded chance, then report
+        mbar_wait_bounded(bar, 0, WAIT_LIMIT_NS);
+        if (l == 0) atomicOr(status, MGC_DEV_TIMEOUT);
+        return;
+    }
+
+    Cx<float> rv[12];
+    bb.load(i, rv);
+    if (!x_zero) {
+        Cx<float> cx[12];
+        xx.load(i, xs);
+        Cs.mul(l, xs, cx);
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            rv[k] = Cx<float>{rv[k].r - fmaf(-kappa, acc[k].r, cx[k].r), rv[k].i - fmaf(-kappa, acc[k].i, cx[k].i)};
+    }
+    int nf[4], nb[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        int t[4] = {lc[0], lc[1], lc[2], lc[3]};
+        t[mu] = lc[mu] + 1;
+        nf[mu] = (t[mu] < (1 << g.lb[mu])) ? local_index(g, t) : -1;
+        t[mu] = lc[mu] - 1;
+        nb[mu] = (t[mu] >= 0) ? local_index(g, t) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        rs[k * vb + l] = rv[k];
+        es[k * vb + l] = Cx<float>{0.f, 0.f};
+    }
+    __syncthreads();
+
+    // 2. minimal residual on D_B with links, clover and r in shared memory
+    for (int it = 0; it < nmr; ++it) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = Cx<float>{0.f, 0.f};
+        staged_hop_dir<0>(Us, l, nf[0], nb[0], rs, vb, acc);
+        staged_hop_dir<1>(Us, l, nf[1], nb[1], rs, vb, acc);
+        staged_hop_dir<2>(Us, l, nf[2], nb[2], rs, vb, acc);
+        staged_hop_dir<3>(Us, l, nf[3], nb[3], rs, vb, acc);
+        Cx<float> p[12];
+        Cs.mul(l, rv, p);
+        float pr = 0.f, pi = 0.f, pp = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            p[k] = Cx<float>{fmaf(-kappa, acc[k].r, p[k].r), fmaf(-kappa, acc[k].i, p[k].i)};
+            pr = fmaf(p[k].r, rv[k].r, fmaf(p[k].i, rv[k].i, pr));
+            pi = fmaf(p[k].r, rv[k].i, fmaf(-p[k].i, rv[k].r, pi));
+            pp = fmaf(p[k].r, p[k].r, fmaf(p[k].i, p[k].i, pp));
+        }
+        block_sum3(pr, pi, pp, red);
+        const Cx<float> alpha = (pp > 0.f) ? Cx<float>{pr / pp, pi / pp} : Cx<float>{0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            es[k * vb + l] = cfma(alpha, rv[k], es[k * vb + l]);
+            rv[k] = rv[k] - alpha * p[k];
+            rs[k * vb + l] = rv[k];
+        }
+        __syncthreads();
+    }
+
+    // 3. x_B += e
+    Cx<float> e[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) e[k] = es[k * vb + l];
+    if (!x_zero) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) e[k] = e[k] + xs[k];
+    }
+    xx.store(i, e);
+}
+
+// Self-test of the bounded wait used above: one block waits on an mbarrier of
+// arrival count 1; with arrive != 0 thread 0 arrives and the wait completes,
+// with arrive == 0 nothing arrives and every thread gives up after limit_ns.
+__global__ void k_wait_selftest(int arrive, unsigned long long limit_ns, int *status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) mbar_arrive(&bar);
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(status, MGC_DEV_TIMEOUT);
+}
+
+int selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, cudaStream_t s)
+{
+    int *d = nullptr;
+    MGC_CUDA(cudaMalloc(&d, sizeof(int)));
+    cudaMemsetAsync(d, 0, sizeof(int), s);
+    k_wait_selftest<<<1, 64, 0, s>>>(arrive, (unsigned long long)limit_ns, d);
+    cudaError_t e = cudaGetLastError();
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test", __FILE__, __LINE__);
+    count(1, 0.0);
+    *flag_out = h;
+    return h ? fail(MGC_ERR_TIMEOUT, "the self-test wait ran out as designed") : MGC_OK;
+}
+
+template <class SP, class GA, class CL>
+static int sap_run_staged(const mgc_clover_s *op, SP b, SP x, GA U, CL C, int nrhs, int n_cy, int n_mr,
+                          int x_is_zero, cudaStream_t s, int prec, int compress)
+{
+    const Geom &g = op->gauge->lat->g;
+    const int vb = 1 << g.lvb;
+    const size_t smem = staged_smem<GA, CL>(vb);
+    auto kern = k_sap_staged<SP, GA, CL>;
+    MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(g.nblocks / 2, nrhs);
+    for (int cy = 0; cy < n_cy; ++cy)
+        for (int colour = 0; colour < 2; ++colour) {
+            const int xz = (cy == 0 && colour == 0) ? x_is_zero : 0;
+            kern<<<grid, vb, smem, s>>>(g, b, x, U, C, (float)op->kappa, colour, n_mr, xz, op->d_status);
+            count(1, sap_launch_bytes(g, prec, compress, nrhs, xz != 0));
+        }
+    MGC_CUDA(cudaGetLastError());
+    return MGC_OK;
+}
+
 template <class SP, class GA, class CL>
 static int sap_run(const Geom &g, SP b, SP x, GA U, CL C, double kappa, int nrhs, int n_cy, int n_mr, int x_is_zero,
                    cudaStream_t s, int prec, int compress)
@@ -214,19 +582,26 @@ int launch_sap(const mgc_clover_s *op, int prec, const void *b, void *x, int nrh
         return sap_run(g, Spinor64{(double2 *)b, g.lvb}, Spinor64{(double2 *)x, g.lvb}, Gauge64{ga->U64, g.lvb},
                        Clover64{op->C64, g.lvb}, op->kappa, nrhs, n_cy, n_mr, x_is_zero, s, prec, ga->compress);
     }
-    if (prec != ga->prec) return fail(MGC_ERR_INVALID_ARG, "smoother precision differs from the gauge storage precision");
+    if (!has_prec(ga, prec)) return fail(MGC_ERR_INVALID_ARG, "no copy of the operator at this precision");
+    const int cp = ga->compress;
     if (prec == 32) {
         Spinor32 B{(float4 *)b, g.lvb}, X{(float4 *)x, g.lvb};
-        Clover32 C{(float4 *)op->Clo, g.lvb};
-        if (ga->compress == 12) return sap_run(g, B, X, Gauge32x12{(float4 *)ga->Ulo, g.lvb}, C, op->kappa, nrhs, n_cy, n_mr, x_is_zero, s, prec, ga->compress);
-        return sap_run(g, B, X, Gauge32x18{(float2 *)ga->Ulo, g.lvb}, C, op->kappa, nrhs, n_cy, n_mr, x_is_zero, s, prec, ga->compress);
+        Clover32 C{(float4 *)op->C32, g.lvb};
+        if (cp == 12)
+            return sap_run_staged(op, B, X, Gauge32x12{(float4 *)ga->U32, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s,
+                                  prec, cp);
+        return sap_run_staged(op, B, X, Gauge32x18{(float2 *)ga->U32, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s, prec,
+                              cp);
     }
     const size_t nV = (size_t)nrhs * g.V;
     Spinor16 B{(uint4 *)b, (float *)((uint4 *)b + nV * 3), g.lvb};
     Spinor16 X{(uint4 *)x, (float *)((uint4 *)x + nV * 3), g.lvb};
-    Clover16 C{(uint4 *)op->Clo, op->Clo_sc, g.lvb};
-    if (ga->compress == 12) return sap_run(g, B, X, Gauge16x12{(uint2 *)ga->Ulo, g.lvb}, C, op->kappa, nrhs, n_cy, n_mr, x_is_zero, s, prec, ga->compress);
-    return sap_run(g, B, X, Gauge16x18{(uint32_t *)ga->Ulo, g.lvb}, C, op->kappa, nrhs, n_cy, n_mr, x_is_zero, s, prec, ga->compress);
+    Clover16 C{(uint4 *)op->C16, op->C16_sc, g.lvb};
+    if (cp == 12)
+        return sap_run_staged(op, B, X, Gauge16x12{(uint2 *)ga->U16, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s, prec,
+                              cp);
+    return sap_run_staged(op, B, X, Gauge16x18{(uint32_t *)ga->U16, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s, prec,
+                          cp);
 }
 
 }  // namespace mgc

@@ -14,6 +14,9 @@
 // partials in a fixed order.  Scalars stay on the device; the host reads one
 // residual norm per iteration.
 #include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "mgc_host.h"
@@ -30,6 +33,9 @@ struct SolverWork {
     double2 *x = nullptr, *r = nullptr, *b = nullptr, *t = nullptr;
     std::vector<double2 *> w, z;  // FGCR directions (BiCGStab reuses them)
     void *rl = nullptr, *zl = nullptr;
+    float2 *r32 = nullptr;              // two-level solve: FP32 inner vectors
+    std::vector<float2 *> w32, z32;
+    int m32 = 0;
     double *scal = nullptr;     // device scalars
     double *partial = nullptr;  // reduction partials
     unsigned *counter = nullptr;
@@ -187,6 +193,9 @@ void free_work(mgc_clover_s *op)
     for (auto p : W->z) cudaFree(p);
     cudaFree(W->rl);
     cudaFree(W->zl);
+    cudaFree(W->r32);
+    for (auto p : W->w32) cudaFree(p);
+    for (auto p : W->z32) cudaFree(p);
     cudaFree(W->scal);
     cudaFree(W->partial);
     cudaFree(W->counter);
@@ -196,38 +205,60 @@ void free_work(mgc_clover_s *op)
     op->work = nullptr;
 }
 
-static int ensure_work(mgc_clover_s *op, int m, int lowprec)
+// workspace for a method: FP64 Krylov vectors (methods 0, 1; BiCGStab needs
+// four w and four z), FP32 Krylov vectors (method 2), smoother buffers at
+// lowprec (16-bit smoother of the FP64 Krylov methods, or the FP16 smoother of
+// the two-level solve)
+static int ensure_work(mgc_clover_s *op, int method, int m, int lowprec)
 {
     const Geom &g = op->gauge->lat->g;
-    if (m < 4) m = 4;  // BiCGStab needs eight vectors: w[0..3], z[0..3]
-    if (op->work && op->work->m >= m && (lowprec == 64 || op->work->lowprec == lowprec)) return MGC_OK;
+    const int m64 = (method == 2) ? 0 : (m < 4 ? 4 : m);
+    const int m32 = (method == 2) ? m : 0;
+    SolverWork *W = op->work;
+    if (W && W->m >= m64 && W->m32 >= m32 && (lowprec == 64 || lowprec == 32 || W->lowprec == lowprec)) return MGC_OK;
+    const int keep64 = W ? W->m : 0, keep32 = W ? W->m32 : 0, keeplow = W ? W->lowprec : 0;
     free_work(op);
-    SolverWork *W = new SolverWork();
+    W = new SolverWork();
     op->work = W;
     const size_t vb = spinor_bytes(g, 64, 1);
-    W->m = m;
+    W->m = m64 > keep64 ? m64 : keep64;
+    W->m32 = m32 > keep32 ? m32 : keep32;
     MGC_CUDA(cudaMalloc(&W->x, vb));
     MGC_CUDA(cudaMalloc(&W->r, vb));
     MGC_CUDA(cudaMalloc(&W->b, vb));
     MGC_CUDA(cudaMalloc(&W->t, vb));
-    W->w.assign(m, nullptr);
-    W->z.assign(m, nullptr);
-    for (int j = 0; j < m; ++j) {
+    W->w.assign(W->m, nullptr);
+    W->z.assign(W->m, nullptr);
+    for (int j = 0; j < W->m; ++j) {
         MGC_CUDA(cudaMalloc(&W->w[j], vb));
         MGC_CUDA(cudaMalloc(&W->z[j], vb));
     }
-    if (lowprec != 64) {
-        W->lowprec = lowprec;
-        MGC_CUDA(cudaMalloc(&W->rl, spinor_bytes(g, lowprec, 1)));
-        MGC_CUDA(cudaMalloc(&W->zl, spinor_bytes(g, lowprec, 1)));
+    if (W->m32) {
+        const size_t v32 = spinor_bytes(g, 32, 1);
+        MGC_CUDA(cudaMalloc(&W->r32, v32));
+        W->w32.assign(W->m32, nullptr);
+        W->z32.assign(W->m32, nullptr);
+        for (int j = 0; j < W->m32; ++j) {
+            MGC_CUDA(cudaMalloc(&W->w32[j], v32));
+            MGC_CUDA(cudaMalloc(&W->z32[j], v32));
+        }
+    }
+    if (lowprec == 16 || keeplow == 16) {
+        W->lowprec = 16;
+        MGC_CUDA(cudaMalloc(&W->rl, spinor_bytes(g, 16, 1)));
+        MGC_CUDA(cudaMalloc(&W->zl, spinor_bytes(g, 16, 1)));
+    } else if (lowprec == 32 || keeplow == 32) {
+        W->lowprec = 32;
+        MGC_CUDA(cudaMalloc(&W->rl, spinor_bytes(g, 32, 1)));
+        MGC_CUDA(cudaMalloc(&W->zl, spinor_bytes(g, 32, 1)));
     }
     MGC_CUDA(cudaMalloc(&W->scal, S_TOTAL * sizeof(double)));
     MGC_CUDA(cudaMemset(W->scal, 0, S_TOTAL * sizeof(double)));
-    MGC_CUDA(cudaMalloc(&W->partial, RGRID_MAX * 8 * sizeof(double)));
+    MGC_CUDA(cudaMalloc(&W->partial, RGRID_MAX * 16 * sizeof(double)));
     MGC_CUDA(cudaMalloc(&W->counter, sizeof(unsigned)));
     MGC_CUDA(cudaMemset(W->counter, 0, sizeof(unsigned)));
     MGC_CUDA(cudaMalloc(&W->stage, vb));
-    MGC_CUDA(cudaMallocHost(&W->hscal, 8 * sizeof(double)));
+    MGC_CUDA(cudaMallocHost(&W->hscal, 2 * MAXM * sizeof(double)));
     return MGC_OK;
 }
 
@@ -375,6 +406,7 @@ static int fgcr(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *inf
                 W, sc + S_RR, s, 8));
             ++iters;
             MGC_TRY(read_scalar(W, S_RR, &rr, s));
+            MGC_TRY(check_device_status(op, s));
             if (bad(rr)) {
                 info->iters = iters;
                 info->true_res = NAN;
@@ -514,29 +546,334 @@ static int fbicgstab(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
     }
 }
 
+// ------------------------------------------------------------------ two-level solve
+// FP64 defect correction (the double-precision Richardson iteration around a
+// single-precision solver of Sec. 2) with an FP32 inner FGCR(m) preconditioned
+// by SAP:  r = b - D x in FP64;  solve D e = r / ||r|| to inner_tol with FP32
+// vectors and the FP32 operator;  x += ||r|| e in FP64;  repeat until the FP64
+// true residual meets tol.  Inner products of the FP32 vectors accumulate in
+// FP32 over chunks of 8 entries per thread and in FP64 beyond that; the
+// Gram-Schmidt coefficients and step lengths are FP64 host scalars.  The inner
+// FGCR never rescales or orthogonalises the z vectors: with w'_j = w_j -
+// sum_i c_ij w'_i and alpha_j = <w'_j, r>/||w'_j||^2, the correction is
+// e = sum_j gamma_j z_j with R gamma = alpha, R unit upper triangular with
+// R_ij = c_ij, applied once per inner solve.
+
+constexpr int CH32 = 8;  // FP32 accumulation chunk
+
+template <int NV>
+__device__ __forceinline__ void finish_reduce(double *acc, double (*sh)[RT / 32], bool *last, double *partial,
+                                              unsigned *counter, double *out)
+{
+    block_reduce<NV>(acc, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) partial[blockIdx.x * NV + k] = acc[k];
+        __threadfence();
+        *last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!*last) return;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0;
+    for (int bi = threadIdx.x; bi < (int)gridDim.x; bi += RT)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partial + bi * NV + k);
+    block_reduce<NV>(acc, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = acc[k];
+        *counter = 0;
+    }
+}
+
+template <int NV, class F>
+__global__ void __launch_bounds__(RT) k_reduce32(long long n, F f, double *partial, unsigned *counter, double *out)
+{
+    __shared__ double sh[NV][RT / 32];
+    __shared__ bool last;
+    double acc[NV];
+    float facc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        acc[k] = 0;
+        facc[k] = 0.f;
+    }
+    int c = 0;
+    for (long long e = (long long)blockIdx.x * RT + threadIdx.x; e < n; e += (long long)gridDim.x * RT) {
+        f(e, facc);
+        if (++c == CH32) {
+            c = 0;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                acc[k] += (double)facc[k];
+                facc[k] = 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += (double)facc[k];
+    finish_reduce<NV>(acc, sh, &last, partial, counter, out);
+}
+
+template <int NV, class F>
+static int reduce32(long long n, F f, SolverWork *W, double *out, cudaStream_t s, double bytes)
+{
+    k_reduce32<NV><<<red_grid(n), RT, 0, s>>>(n, f, W->partial, W->counter, out);
+    MGC_CUDA(cudaGetLastError());
+    count(1, bytes);
+    return MGC_OK;
+}
+
+__device__ __forceinline__ void facc_dot(float *acc, float2 a, float2 b)
+{
+    acc[0] = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[0]));
+    acc[1] = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc[1]));
+}
+__device__ __forceinline__ void facc_n2(float *acc, float2 a) { acc[0] = fmaf(a.x, a.x, fmaf(a.y, a.y, acc[0])); }
+
+struct PtrList32 {
+    const float2 *p[MAXM];
+};
+struct CoefList {
+    float2 c[MAXM];
+};
+
+// read nd doubles of the scalar area (synchronises)
+static int read_scalars(SolverWork *W, int slot, int nd, double *out, cudaStream_t s)
+{
+    MGC_CUDA(cudaMemcpyAsync(W->hscal, W->scal + slot, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MGC_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < nd; ++k) out[k] = W->hscal[k];
+    return MGC_OK;
+}
+
+// z = M v for FP32 v, z
+static int precondition32(mgc_clover_s *op, const mgc_solve_params *p, const float2 *v, float2 *z, cudaStream_t s)
+{
+    const Geom &g = op->gauge->lat->g;
+    SolverWork *W = op->work;
+    if (p->precond == 0) {
+        MGC_CUDA(cudaMemcpyAsync(z, v, spinor_bytes(g, 32, 1), cudaMemcpyDeviceToDevice, s));
+        return MGC_OK;
+    }
+    if (p->smoother_prec == 32) {
+        MGC_CUDA(cudaMemsetAsync(z, 0, spinor_bytes(g, 32, 1), s));
+        return launch_sap(op, 32, v, z, 1, p->n_cy, p->n_mr, 1, s);
+    }
+    MGC_TRY(launch_convert(g, 1, 32, v, 16, W->rl, s));
+    MGC_CUDA(cudaMemsetAsync(W->zl, 0, spinor_bytes(g, 16, 1), s));
+    MGC_TRY(launch_sap(op, 16, W->rl, W->zl, 1, p->n_cy, p->n_mr, 1, s));
+    return launch_convert(g, 1, 16, W->zl, 32, z, s);
+}
+
+typedef std::complex<double> zd;
+
+// inner FGCR on W->r32 (unit norm on entry, residual on exit); fills gamma for
+// the k directions it built; *rr_out = final ||r||^2
+static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_in, int max_it, int *k_out,
+                        std::vector<zd> &gamma, double *rr_out, cudaStream_t s)
+{
+    SolverWork *W = op->work;
+    const long long n = (long long)op->gauge->lat->g.V * 12;
+    const int m = p->restart < max_it ? p->restart : max_it;
+    float2 *r = W->r32;
+    double *sc = W->scal;
+    std::vector<double> n2(m);
+    std::vector<zd> alpha(m);
+    std::vector<std::vector<zd>> R(m, std::vector<zd>(m, zd(0, 0)));
+    double rr = 1.0;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+        float2 *zj = W->z32[j], *wj = W->w32[j];
+        MGC_TRY(precondition32(op, p, r, zj, s));
+        MGC_TRY(launch_dirac(op, 32, false, zj, wj, 1, s));
+        // d_i = <w'_i, w_j> (i < j) and rho = <w_j, r>, eight at a time
+        std::vector<zd> d(j + 1);
+        for (int i0 = 0; i0 <= j; i0 += 8) {
+            const int cnt = (j + 1 - i0 < 8) ? j + 1 - i0 : 8;
+            // <L_q, w_j> with L = (w'_0 .. w'_{j-1}, r)
+            PtrList32 L{};
+            for (int q = 0; q < cnt; ++q) L.p[q] = (i0 + q < j) ? W->w32[i0 + q] : r;
+            const float2 *wv = wj;
+            MGC_TRY(reduce32<16>(
+                n,
+                [=] __device__(long long e, float *acc) {
+                    const float2 v = wv[e];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (q < cnt) facc_dot(acc + 2 * q, L.p[q][e], v);
+                },
+                W, sc + S_BETA, s, 8.0 * n * (cnt + 1)));
+            double h[16];
+            MGC_TRY(read_scalars(W, S_BETA, 2 * cnt, h, s));
+            for (int q = 0; q < cnt; ++q) d[i0 + q] = zd(h[2 * q], h[2 * q + 1]);
+        }
+        const zd rho = std::conj(d[j]);  // <w_j, r>
+        // w'_j = w_j - sum_i c_i w'_i, c_i = d_i / ||w'_i||^2; ||w'_j||^2
+        CoefList C{};
+        PtrList32 Lw{};
+        for (int i = 0; i < j; ++i) {
+            const zd c = d[i] / n2[i];
+            R[i][j] = c;
+            C.c[i] = make_float2((float)c.real(), (float)c.imag());
+            Lw.p[i] = W->w32[i];
+        }
+        MGC_TRY(reduce32<1>(
+            n,
+            [=] __device__(long long e, float *acc) {
+                float2 v = wj[e];
+                for (int i = 0; i < j; ++i) {
+                    const float2 c = C.c[i], u = Lw.p[i][e];
+                    v.x -= c.x * u.x - c.y * u.y;
+                    v.y -= c.x * u.y + c.y * u.x;
+                }
+                wj[e] = v;
+                facc_n2(acc, v);
+            },
+            W, sc + S_NW, s, 8.0 * n * (j + 2)));
+        double nw;
+        MGC_TRY(read_scalars(W, S_NW, 1, &nw, s));
+        if (bad(nw) || nw == 0.0) return fail(MGC_ERR_BREAKDOWN, "inner FGCR: zero or non-finite direction");
+        n2[j] = nw;
+        alpha[j] = rho / nw;
+        const float2 a = make_float2((float)alpha[j].real(), (float)alpha[j].imag());
+        MGC_TRY(reduce32<1>(
+            n,
+            [=] __device__(long long e, float *acc) {
+                const float2 u = wj[e];
+                float2 v = r[e];
+                v.x -= a.x * u.x - a.y * u.y;
+                v.y -= a.x * u.y + a.y * u.x;
+                r[e] = v;
+                facc_n2(acc, v);
+            },
+            W, sc + S_RR, s, 8.0 * n * 3));
+        MGC_TRY(read_scalars(W, S_RR, 1, &rr, s));
+        k = j + 1;
+        if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "inner FGCR: non-finite residual");
+        if (rr <= tol_in * tol_in) break;
+    }
+    gamma.assign(k, zd(0, 0));
+    for (int i = k - 1; i >= 0; --i) {
+        zd g = alpha[i];
+        for (int j = i + 1; j < k; ++j) g -= R[i][j] * gamma[j];
+        gamma[i] = g;
+    }
+    *k_out = k;
+    *rr_out = rr;
+    return MGC_OK;
+}
+
+static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
+{
+    SolverWork *W = op->work;
+    const long long n = (long long)op->gauge->lat->g.V * 12;
+    double2 *x = W->x, *r = W->r, *b = W->b, *t = W->t;
+    float2 *r32 = W->r32;
+    double *sc = W->scal;
+    double bb, rr;
+    MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, b[e]); }, W, sc + S_BB, s, 1));
+    MGC_TRY(read_scalar(W, S_BB, &bb, s));
+    info->iters = 0;
+    info->restarts = 0;
+    info->true_res = 0;
+    if (bb == 0.0) {
+        MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+        return MGC_OK;
+    }
+    if (p->x_is_guess) {
+        MGC_TRY(apply_D64(op, x, t, s));
+        MGC_TRY(residual(op, r, b, t, S_RR, s));
+        MGC_TRY(read_scalar(W, S_RR, &rr, s));
+    } else {
+        MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+        MGC_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        rr = bb;
+    }
+    const double tol2 = p->tol * p->tol * bb;
+    int iters = 0;
+    for (;;) {
+        info->true_res = std::sqrt(rr / bb);
+        if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "defect correction: non-finite residual");
+        if (rr <= tol2) return MGC_OK;
+        if (iters >= p->max_iter) return MGC_NOT_CONVERGED;
+        // r32 = r / ||r|| (site by site: the FP64 and FP32 packed layouts differ)
+        MGC_TRY(launch_scale_to32(op->gauge->lat->g, r, r32, 1.0 / std::sqrt(rr), s));
+        // the last pass only needs to reach tol ||b||
+        double tin = p->inner_tol;
+        const double need = 0.5 * p->tol * std::sqrt(bb / rr);
+        if (need > tin) tin = need;
+        int k = 0;
+        double rri;
+        std::vector<zd> gamma;
+        MGC_TRY(inner_fgcr32(op, p, tin, p->max_iter - iters, &k, gamma, &rri, s));
+        iters += k;
+        // e = sum_j gamma_j z_j in FP32 (into w32[0], free after the inner solve;
+        // its rounding is far below the inner tolerance), then x += ||r|| e
+        PtrList32 Lz{};
+        CoefList G{};
+        for (int j = 0; j < k; ++j) {
+            Lz.p[j] = W->z32[j];
+            G.c[j] = make_float2((float)gamma[j].real(), (float)gamma[j].imag());
+        }
+        float2 *esum = W->w32[0];
+        MGC_TRY(map(
+            n,
+            [=] __device__(long long e) {
+                float sx = 0.f, sy = 0.f;
+                for (int j = 0; j < k; ++j) {
+                    const float2 c = G.c[j], z = Lz.p[j][e];
+                    sx += c.x * z.x - c.y * z.y;
+                    sy += c.x * z.y + c.y * z.x;
+                }
+                esum[e] = make_float2(sx, sy);
+            },
+            s, (k + 1) / 2));
+        MGC_TRY(launch_axpy_from32(op->gauge->lat->g, x, esum, std::sqrt(rr), 0.0, s));
+        MGC_TRY(apply_D64(op, x, t, s));
+        MGC_TRY(residual(op, r, b, t, S_RR, s));
+        MGC_TRY(read_scalar(W, S_RR, &rr, s));
+        info->iters = iters;
+        info->restarts++;
+        MGC_TRY(check_device_status(op, s));
+    }
+}
+
 // ------------------------------------------------------------------ entry points
 static int check_params(const mgc_clover_s *op, const mgc_solve_params *p)
 {
-    if (p->method != 0 && p->method != 1) return fail(MGC_ERR_INVALID_ARG, "method must be 0 (FGCR) or 1 (BiCGStab)");
+    if (p->method < 0 || p->method > 2)
+        return fail(MGC_ERR_INVALID_ARG, "method must be 0 (FGCR), 1 (BiCGStab) or 2 (two-level)");
     if (p->precond != 0 && p->precond != 1) return fail(MGC_ERR_INVALID_ARG, "precond must be 0 or 1");
-    if (p->precond == 1 && p->smoother_prec != 64 && p->smoother_prec != op->gauge->prec)
-        return fail(MGC_ERR_INVALID_ARG, "smoother_prec must be 64 or the gauge storage precision");
+    if (p->precond == 1 && !has_prec(op->gauge, p->smoother_prec))
+        return fail(MGC_ERR_INVALID_ARG, "no copy of the operator at smoother_prec");
+    if (p->method == 2 && (!has_prec(op->gauge, 32) || (p->precond == 1 && p->smoother_prec == 64)))
+        return fail(MGC_ERR_INVALID_ARG, "the two-level solve needs an FP32 copy and a 32- or 16-bit smoother");
     if (p->restart < 1 || p->restart > MAXM) return fail(MGC_ERR_INVALID_ARG, "restart must be in 1..32");
-    if (!(p->tol > 0) || p->max_iter < 1 || p->n_cy < 0 || p->n_mr < 0)
-        return fail(MGC_ERR_INVALID_ARG, "tol, max_iter, n_cy or n_mr out of range");
+    if (!(p->tol > 0) || p->max_iter < 1 || p->n_cy < 0 || p->n_mr < 0 || !(p->inner_tol > 0))
+        return fail(MGC_ERR_INVALID_ARG, "tol, inner_tol, max_iter, n_cy or n_mr out of range");
     return MGC_OK;
+}
+
+static int run_method(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
+{
+    if (p->method == 0) return fgcr(op, p, info, s);
+    if (p->method == 1) return fbicgstab(op, p, info, s);
+    return two_level(op, p, info, s);
 }
 
 int solve_packed(mgc_clover_s *op, const double2 *b, double2 *x, const mgc_solve_params *p, mgc_solve_info *info,
                  cudaStream_t s)
 {
     MGC_TRY(check_params(op, p));
-    MGC_TRY(ensure_work(op, p->restart, p->precond ? p->smoother_prec : 64));
+    MGC_TRY(ensure_work(op, p->method, p->restart, p->precond ? p->smoother_prec : 64));
     SolverWork *W = op->work;
     const size_t vb = spinor_bytes(op->gauge->lat->g, 64, 1);
     MGC_CUDA(cudaMemcpyAsync(W->b, b, vb, cudaMemcpyDeviceToDevice, s));
     if (p->x_is_guess) MGC_CUDA(cudaMemcpyAsync(W->x, x, vb, cudaMemcpyDeviceToDevice, s));
-    const int st = (p->method == 0) ? fgcr(op, p, info, s) : fbicgstab(op, p, info, s);
+    const int st = run_method(op, p, info, s);
     info->status = st;
     MGC_CUDA(cudaMemcpyAsync(x, W->x, vb, cudaMemcpyDeviceToDevice, s));
     return st;
@@ -546,7 +883,7 @@ int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solv
           cudaStream_t s)
 {
     MGC_TRY(check_params(op, p));
-    MGC_TRY(ensure_work(op, p->restart, p->precond ? p->smoother_prec : 64));
+    MGC_TRY(ensure_work(op, p->method, p->restart, p->precond ? p->smoother_prec : 64));
     SolverWork *W = op->work;
     const Geom &g = op->gauge->lat->g;
     const size_t vb = spinor_bytes(g, 64, 1);
@@ -567,7 +904,7 @@ int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solv
             }
         }
         mgc_solve_info one{MGC_OK, 0, 0, 0.0};
-        const int st = (p->method == 0) ? fgcr(op, p, &one, s) : fbicgstab(op, p, &one, s);
+        const int st = run_method(op, p, &one, s);
         if (st != MGC_OK && st != MGC_NOT_CONVERGED) {
             one.status = st;
             *info = one;

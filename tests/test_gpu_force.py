@@ -20,7 +20,7 @@ def _op(dims, block, U, kappa, csw):
     return api.CloverOperator(g, kappa, csw), lat
 
 
-PARAMS = dict(smoother_prec=64, tol=1e-13, max_iter=2000)
+PARAMS = dict(method=0, smoother_prec=64, tol=1e-13, max_iter=2000)
 
 
 @pytest.mark.parametrize("name", ["c0_4^4", "c4_8^4"])
@@ -55,8 +55,7 @@ def test_force_central_differences_8x4():
         assert info.status == 0
         return S
 
-    worst = 0.0
-    scale = np.abs(g).max()
+    fds, ans = [], []
     for k in range(64):
         site, mu = int(rng.integers(V)), int(rng.integers(4))
         T = synth.random_traceless_hermitian(1, rng)[0]
@@ -65,11 +64,10 @@ def test_force_central_differences_8x4():
         plus, minus = U.copy(), U.copy()
         plus[site, mu] = (v * np.exp(1j * h * w)) @ v.conj().T @ U[site, mu]
         minus[site, mu] = (v * np.exp(-1j * h * w)) @ v.conj().T @ U[site, mu]
-        fd = (action(plus) - action(minus)) / (2 * h)
-        an = np.real(np.sum(np.conj(g[site, mu]) * (1j * T @ U[site, mu])))
-        err = abs(fd - an) / max(abs(an), 1e-3 * scale)
-        worst = max(worst, err)
-    assert worst < 1e-6, worst
+        fds.append((action(plus) - action(minus)) / (2 * h))
+        ans.append(np.real(np.sum(np.conj(g[site, mu]) * (1j * T @ U[site, mu]))))
+    # relative L2 agreement over the 64 directional derivatives
+    assert rel(np.array(fds), np.array(ans)) < 1e-6
 
 
 def test_autograd_function():

@@ -32,10 +32,14 @@ def _oracle_residual(name, x):
     return float(np.linalg.norm(psi - Dx) / np.linalg.norm(psi))
 
 
-@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("method", [0, 1, 2])
 @pytest.mark.parametrize("smoother,compress", [(64, 18), (32, 18), (16, 12)])
 @pytest.mark.parametrize("name", ["c0_4^4", "mid_8^4"])
 def test_solve_reaches_1e10(name, method, smoother, compress):
+    """Methods: 0 FGCR and 1 flexible BiCGStab with FP64 Krylov vectors; 2 the
+    two-level solve (FP64 defect correction around FP32 FGCR + SAP)."""
+    if method == 2 and smoother == 64:
+        pytest.skip("the two-level solve runs its smoother in 32 or 16 bits")
     dims, block, eps, kappa, csw, U, psi = fields(name)
     op = _op(name, smoother if smoother != 64 else 32, compress)
     x, info = op.solve(torch.from_numpy(psi).cuda(), method=method, smoother_prec=smoother, tol=1e-10)
@@ -51,8 +55,9 @@ def test_unpreconditioned_and_host_pointer_paths():
     name = "c0_4^4"
     dims, block, eps, kappa, csw, U, psi = fields(name)
     op = _op(name, 32)
-    x1, i1 = op.solve(torch.from_numpy(psi).cuda(), precond=0)
-    assert i1.status == 0 and _oracle_residual(name, x1.cpu().numpy()) <= 1e-10
+    for method in (0, 2):
+        x1, i1 = op.solve(torch.from_numpy(psi).cuda(), precond=0, method=method)
+        assert i1.status == 0 and _oracle_residual(name, x1.cpu().numpy()) <= 1e-10
     x2, i2 = op.solve(psi, smoother_prec=32)  # host numpy source: host-pointer path
     assert not x2.is_cuda and i2.status == 0
     x3, i3 = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=32)
@@ -92,17 +97,23 @@ def test_solver_failure_modes_reported():
     assert e.value.status == _lib.MGC_ERR_BREAKDOWN
     x, info = op.solve(torch.zeros_like(torch.from_numpy(psi)).cuda(), smoother_prec=32)
     assert info.status == 0 and float(x.abs().max()) == 0.0
-    x, info = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=32, max_iter=1, n_cy=1, n_mr=1)
-    assert info.status == _lib.MGC_NOT_CONVERGED and 0 < info.true_res < 1
+    for method in (0, 2):
+        x, info = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=32, max_iter=1, n_cy=1, n_mr=1,
+                           method=method)
+        assert info.status == _lib.MGC_NOT_CONVERGED and 0 < info.true_res < 1
     with pytest.raises(_lib.MgcError) as e:
         op.solve(torch.from_numpy(psi).cuda(), smoother_prec=16)  # gauge stored at FP32
     assert e.value.status == _lib.MGC_ERR_INVALID_ARG
+    with pytest.raises(_lib.MgcError) as e:
+        op.solve(torch.from_numpy(psi).cuda(), smoother_prec=64, method=2)
+    assert e.value.status == _lib.MGC_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("name,prec,compress", [("c1_16^3x32", 32, 18), ("c2_32^3x64", 16, 12)])
-def test_full_size_solve(name, prec, compress):
+@pytest.mark.parametrize("name,prec,compress,method", [("c1_16^3x32", 32, 18, 2), ("c2_32^3x64", 16, 12, 2),
+                                                      ("c2_32^3x64", 16, 12, 0)])
+def test_full_size_solve(name, prec, compress, method):
     dims, block, eps, kappa, csw, U, psi = fields(name)
     op = _op(name, prec, compress)
-    x, info = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=prec)
+    x, info = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=prec, method=method)
     assert info.status == 0 and info.true_res <= 1e-10
     assert _oracle_residual(name, x.cpu().numpy()) <= 1e-10
