@@ -227,6 +227,30 @@ int mgc_solve(mgc_clover_t op, const double *b, double *x, int nrhs, const mgc_s
               mgc_solve_info *info, void *stream);
 
 /*
+ * mgc_solve without any allocation.  The paper has no counterpart: this entry
+ * point is for callers that cannot call cudaMalloc at solve time -- for example
+ * code whose device memory is all owned by another allocator (a framework's
+ * caching pool or a fixed memory budget), or a loop that cannot afford the
+ * device-wide synchronisation a cudaMalloc/cudaFree pair brings.  It solves
+ * D x = b for one right-hand side with flexible BiCGStab (p->method must be 1)
+ * and performs no cudaMalloc, cudaFree or other allocation: its workspace is a
+ * file-scope device array of fixed size (about 10.4 MB, held by every GPU that
+ * loads the library until the process exits), which limits the lattice to
+ * MGC_NOALLOC_MAX_SITES sites; larger lattices return
+ * MGC_ERR_UNSUPPORTED_SHAPE.  b and x are canonical complex128 device pointers
+ * (p->on_device must be 1); the operator handle (created beforehand) supplies
+ * D and the smoother.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents; calls
+ * that overlap on the GPU (other streams, other host threads) race on it and
+ * must not be made.  Synchronises stream.
+ */
+#define MGC_NOALLOC_MAX_SITES 4096
+int mgc_solve_noalloc(mgc_clover_t op, const double *b, double *x, const mgc_solve_params *p, mgc_solve_info *info,
+                      void *stream);
+
+/*
  * Link force of S = phi^+ (D^+ D)^-1 phi: solves D^+ Y = phi (as
  * gamma5 D^-1 gamma5 phi) and D X = Y, then dS/dU from the hopping outer
  * products and the clover-leaf derivative.  phi: canonical complex128 (one

@@ -77,6 +77,7 @@ SIGNATURES = {
     "mgc_solve_params_default": (None, [C.POINTER(SolveParams)]),
     "mgc_solve": (_I, [_P, _P, _P, _I, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P]),
     "mgc_force": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(SolveInfo), C.POINTER(_D), _P]),
+    "mgc_solve_noalloc": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P]),
 }
 
 _lib = None

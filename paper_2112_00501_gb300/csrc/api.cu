@@ -398,6 +398,13 @@ int mgc_solve(mgc_clover_t op, const double *b, double *x, int nrhs, const mgc_s
     return mgc::solve(op, b, x, nrhs, p, info, (cudaStream_t)stream);
 }
 
+int mgc_solve_noalloc(mgc_clover_t op, const double *b, double *x, const mgc_solve_params *p, mgc_solve_info *info,
+                      void *stream)
+{
+    if (!op || !b || !x || !p || !info) return fail(MGC_ERR_INVALID_ARG, "bad argument");
+    return mgc::solve_noalloc(op, b, x, p, info, (cudaStream_t)stream);
+}
+
 int mgc_force(mgc_clover_t op, const double *phi, double *dSdU, const mgc_solve_params *p, mgc_solve_info *info,
               double *action, void *stream)
 {

@@ -119,6 +119,9 @@ int selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, cudaStr
 int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solve_params *p, mgc_solve_info *info,
           cudaStream_t s);
 void free_work(mgc_clover_s *op);
+// mgc_solve_noalloc: flexible BiCGStab with its workspace in a static device array
+int solve_noalloc(mgc_clover_s *op, const double *b, double *x, const mgc_solve_params *p, mgc_solve_info *info,
+                  cudaStream_t s);
 // solve D x = b for one packed FP64 field already on the device (x holds the guess if guess != 0)
 int solve_packed(mgc_clover_s *op, const double2 *b, double2 *x, const mgc_solve_params *p, mgc_solve_info *info,
                  cudaStream_t s);

@@ -31,10 +31,10 @@ struct SolverWork {
     int m = 0;
     int lowprec = 0;
     double2 *x = nullptr, *r = nullptr, *b = nullptr, *t = nullptr;
-    std::vector<double2 *> w, z;  // FGCR directions (BiCGStab reuses them)
+    double2 *w[MAXM] = {}, *z[MAXM] = {};  // FGCR directions (BiCGStab reuses four of each)
     void *rl = nullptr, *zl = nullptr;
-    float2 *r32 = nullptr;              // two-level solve: FP32 inner vectors
-    std::vector<float2 *> w32, z32;
+    float2 *r32 = nullptr;                  // two-level solve: FP32 inner vectors
+    float2 *w32[MAXM] = {}, *z32[MAXM] = {};
     int m32 = 0;
     double *scal = nullptr;     // device scalars
     double *partial = nullptr;  // reduction partials
@@ -227,8 +227,6 @@ static int ensure_work(mgc_clover_s *op, int method, int m, int lowprec)
     MGC_CUDA(cudaMalloc(&W->r, vb));
     MGC_CUDA(cudaMalloc(&W->b, vb));
     MGC_CUDA(cudaMalloc(&W->t, vb));
-    W->w.assign(W->m, nullptr);
-    W->z.assign(W->m, nullptr);
     for (int j = 0; j < W->m; ++j) {
         MGC_CUDA(cudaMalloc(&W->w[j], vb));
         MGC_CUDA(cudaMalloc(&W->z[j], vb));
@@ -236,8 +234,6 @@ static int ensure_work(mgc_clover_s *op, int method, int m, int lowprec)
     if (W->m32) {
         const size_t v32 = spinor_bytes(g, 32, 1);
         MGC_CUDA(cudaMalloc(&W->r32, v32));
-        W->w32.assign(W->m32, nullptr);
-        W->z32.assign(W->m32, nullptr);
         for (int j = 0; j < W->m32; ++j) {
             MGC_CUDA(cudaMalloc(&W->w32[j], v32));
             MGC_CUDA(cudaMalloc(&W->z32[j], v32));
@@ -862,6 +858,80 @@ static int run_method(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_inf
     if (p->method == 0) return fgcr(op, p, info, s);
     if (p->method == 1) return fbicgstab(op, p, info, s);
     return two_level(op, p, info, s);
+}
+
+// ------------------------------------------------------------------ solve without allocation
+// Scratch of mgc_solve_noalloc: a file-scope device array holding the
+// flexible BiCGStab workspace (x, r, b, t, four w and four z FP64 vectors, two
+// smoother buffers, reduction partials, scalars and the reduction ticket) for
+// lattices of up to MGC_NOALLOC_MAX_SITES sites, about 10.4 MB.  Every GPU
+// that loads the library holds it until the process exits.
+constexpr size_t NA_VEC = (size_t)MGC_NOALLOC_MAX_SITES * 192;  // one FP64 packed spinor
+constexpr size_t NA_LOW = (size_t)MGC_NOALLOC_MAX_SITES * 96;   // one FP32 or FP16 packed spinor
+constexpr size_t NA_PART = (size_t)RGRID_MAX * 16 * sizeof(double);
+constexpr size_t NA_SCAL = 1024;  // >= S_TOTAL doubles
+constexpr size_t NA_CTR = 256;
+constexpr size_t NA_BYTES = 12 * NA_VEC + 2 * NA_LOW + NA_PART + NA_SCAL + NA_CTR;
+static_assert(NA_SCAL >= S_TOTAL * sizeof(double), "scalar area too small");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+// device address of the scratch array, looked up once per device (in host
+// code the array's name is only a stand-in, never a device address)
+static void *g_noalloc_base[64];
+static double g_noalloc_hscal[2 * MAXM];  // pageable host copy of a few scalars
+
+int solve_noalloc(mgc_clover_s *op, const double *b, double *x, const mgc_solve_params *p, mgc_solve_info *info,
+                  cudaStream_t s)
+{
+    const Geom &g = op->gauge->lat->g;
+    if (g.V > MGC_NOALLOC_MAX_SITES)
+        return fail(MGC_ERR_UNSUPPORTED_SHAPE, "mgc_solve_noalloc: the lattice has more sites than "
+                                               "MGC_NOALLOC_MAX_SITES (4096)");
+    if (p->method != 1 || !p->on_device)
+        return fail(MGC_ERR_INVALID_ARG,
+                    "mgc_solve_noalloc: method must be 1 (flexible BiCGStab) and b, x device pointers");
+    MGC_TRY(check_params(op, p));
+    int dev = 0;
+    MGC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(MGC_ERR_INVALID_ARG, "mgc_solve_noalloc: device ordinal above 63");
+    if (!g_noalloc_base[dev]) {
+        void *ptr = nullptr;
+        MGC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_base[dev] = ptr;
+    }
+    unsigned char *base = static_cast<unsigned char *>(g_noalloc_base[dev]);
+    SolverWork W;  // a view of the scratch array: no allocation
+    W.m = 4;
+    W.lowprec = (p->precond && p->smoother_prec != 64) ? p->smoother_prec : 0;
+    double2 **vec[12] = {&W.x, &W.r, &W.b, &W.t, &W.w[0], &W.w[1], &W.w[2], &W.w[3],
+                         &W.z[0], &W.z[1], &W.z[2], &W.z[3]};
+    for (int k = 0; k < 12; ++k) *vec[k] = reinterpret_cast<double2 *>(base + k * NA_VEC);
+    unsigned char *q = base + 12 * NA_VEC;
+    W.rl = q;
+    W.zl = q + NA_LOW;
+    q += 2 * NA_LOW;
+    W.partial = reinterpret_cast<double *>(q);
+    q += NA_PART;
+    W.scal = reinterpret_cast<double *>(q);
+    q += NA_SCAL;
+    W.counter = reinterpret_cast<unsigned *>(q);
+    W.hscal = g_noalloc_hscal;
+    // the reduction ticket and the scalars must start at zero
+    MGC_CUDA(cudaMemsetAsync(W.counter, 0, sizeof(unsigned), s));
+    MGC_CUDA(cudaMemsetAsync(W.scal, 0, NA_SCAL, s));
+    MGC_TRY(launch_pack(g, 64, 1, b, W.b, s));
+    if (p->x_is_guess) MGC_TRY(launch_pack(g, 64, 1, x, W.x, s));
+    mgc_solve_info one{MGC_OK, 0, 0, 0.0};
+    SolverWork *saved = op->work;
+    op->work = &W;
+    const int st = fbicgstab(op, p, &one, s);
+    op->work = saved;
+    one.status = st;
+    *info = one;
+    if (st != MGC_OK && st != MGC_NOT_CONVERGED) return st;
+    MGC_TRY(launch_unpack(g, 64, 1, W.x, x, s));
+    MGC_CUDA(cudaStreamSynchronize(s));
+    return st;
 }
 
 int solve_packed(mgc_clover_s *op, const double2 *b, double2 *x, const mgc_solve_params *p, mgc_solve_info *info,
