@@ -199,9 +199,10 @@ class CloverOperator:
         self.sap_smooth(bp, xp, prec, nrhs, n_cy, n_mr, x_is_zero=x0 is None)
         return self.lattice.unpack(xp, prec, nrhs)
 
-    def solve(self, b, params: SolveParams | None = None, x0=None, stream=None, **kw):
+    def solve(self, b, params: SolveParams | None = None, x0=None, stream=None, out=None, **kw):
         """Solve D x = b.  b: canonical complex128 on the GPU (on_device = 1) or a
-        host tensor / array (on_device = 0).  Returns (x, info)."""
+        host tensor / array (on_device = 0).  `out` (optional) receives x and
+        must live where b lives (pinned for host b).  Returns (x, info)."""
         p = params if params is not None else solve_params(**kw)
         host = not (isinstance(b, torch.Tensor) and b.is_cuda)
         if host:
@@ -215,6 +216,11 @@ class CloverOperator:
         if x0 is not None:
             x = _canon(x0, bt.device).clone()
             p.x_is_guess = 1
+        elif out is not None:
+            if out.shape != bt.shape or out.dtype != torch.complex128 or out.device != bt.device:
+                raise ValueError("out must match b in shape, dtype and device")
+            x = out
+            p.x_is_guess = 0
         else:
             x = torch.zeros_like(bt)
             if host:
