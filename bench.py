@@ -430,7 +430,7 @@ def main():
                       "frac_hbm": (bytes_launch / t_launch / 1e9 / hbm) if hbm else None,
                       "tflops_fp32": sap_tflops, "frac_fp32_peak": sap_tflops / FP32_FMA_PEAK_TFLOPS},
         "roofline": {
-            "kernel": "k_sap_colour (FP16 storage, 12-real links)",
+            "kernel": "k_sap_h16 (FP16 storage, 12-real links, 4^4 domains)",
             "bound": "hbm",
             "achieved": bytes_launch / t_launch / 1e9,
             "peak": hbm,

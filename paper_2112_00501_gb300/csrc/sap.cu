@@ -502,6 +502,248 @@ __global__ void __launch_bounds__(256, 2) k_sap_staged(Geom g, SP b, SP x, GA U,
     xx.store(i, e);
 }
 
+// ------------------------------------------------------------------ FP16-storage kernel
+// The benchmark format (FP16 fields with per-site scales) for 2^4 and 4^4
+// domains, with the domain size known at compile time.  Shared memory holds
+// the domain's links as 18-real FP16 (a 12-real copy is brought in by TMA into
+// the r area and expanded once, so the MR steps never rebuild row 2), the FP16
+// clover term with its scales, and r as pairs of complex numbers.  e stays in
+// registers; a thread re-reads its own r from shared memory when it needs it.
+// About 100 KB of shared memory: two blocks per SM.
+
+template <class GA> struct H16Links;
+template <> struct H16Links<Gauge16x12> {
+    static constexpr bool EXPAND = true;
+    static constexpr int STAGE = 96;  // bytes per site of the staged copy
+    static __device__ const void *src(const Gauge16x12 &U, int blk, int lvb) { return U.p + ((size_t)blk * 12 << lvb); }
+};
+template <> struct H16Links<Gauge16x18> {
+    static constexpr bool EXPAND = false;
+    static constexpr int STAGE = 144;
+    static __device__ const void *src(const Gauge16x18 &U, int blk, int lvb) { return U.p + ((size_t)blk * 36 << lvb); }
+};
+
+template <int LVB>
+__host__ __device__ constexpr size_t h16_smem_bytes()
+{
+    return (size_t)(1 << LVB) * (144 + 144 + 4 + 96) + 96 * 4 + 16;
+}
+
+template <int MU, int SGN, int VB>
+__device__ __forceinline__ void h16_hop(const float4 *rs, int n, const uint32_t *sL, int lk, Cx<float> acc[12])
+{
+    Cx<float> s[12], h[6], w[6], u[9];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float4 v = rs[k * VB + n];
+        s[2 * k] = {v.x, v.y};
+        s[2 * k + 1] = {v.z, v.w};
+    }
+    project<MU, SGN>(s, h);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float2 v = unpack_half2(sL[(MU * 9 + k) * VB + lk]);
+        u[k] = {v.x, v.y};
+    }
+    if (SGN < 0) su3_mul(u, h, w);
+    else su3_dag_mul(u, h, w);
+    reconstruct_add<MU, SGN>(acc, w);
+}
+
+template <int LVB, class GA>
+__global__ void __launch_bounds__(1 << LVB, 2) k_sap_h16(Geom g, Spinor16 b, Spinor16 x, GA U, Clover16 C, float kappa,
+                                                         int colour, int nmr, int x_zero, int *status)
+{
+    constexpr int VB = 1 << LVB;
+    constexpr int LB = LVB / 4;
+    using HL = H16Links<GA>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint32_t *sL = reinterpret_cast<uint32_t *>(smem);        // [4][9][VB] half2
+    uint4 *sC = reinterpret_cast<uint4 *>(sL + 36 * VB);      // [9][VB]
+    float *sS = reinterpret_cast<float *>(sC + 9 * VB);       // [VB]
+    float4 *rs = reinterpret_cast<float4 *>(sS + VB);         // [6][VB]; first the 12-real link stage
+    float *red = reinterpret_cast<float *>(rs + 6 * VB);      // 96 floats
+    uint64_t *bar = reinterpret_cast<uint64_t *>(red + 96);
+
+    // geometry with the domain extents as compile-time constants
+    Geom gg = g;
+    gg.lvb = LVB;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) gg.lb[mu] = LB;
+    const int rr = blockIdx.y;
+    Spinor16 bb = shift_rhs(b, rr, g.V), xx = shift_rhs(x, rr, g.V);
+    bb.lvb = LVB;
+    xx.lvb = LVB;
+    GA Ug = U;
+    Ug.lvb = LVB;
+    int j = blockIdx.x;
+    const int half0 = g.NB[0] >> 1;
+    int bc[4];
+    const int m = j % half0;
+    j /= half0;
+    bc[1] = j % g.NB[1];
+    j /= g.NB[1];
+    bc[2] = j % g.NB[2];
+    bc[3] = j / g.NB[2];
+    bc[0] = 2 * m + ((colour + bc[1] + bc[2] + bc[3]) & 1);
+    const int blk = block_index(gg, bc);
+    const int l = threadIdx.x;
+    const int i = (blk << LVB) | l;
+
+    if (l == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (l == 0) {
+        const unsigned lbytes = HL::STAGE * VB, cb = 144 * VB, sb = 4 * VB;
+        mbar_arrive_expect_tx(bar, lbytes + cb + sb);
+        bulk_g2s(HL::EXPAND ? (void *)rs : (void *)sL, HL::src(U, blk, LVB), lbytes, bar);
+        bulk_g2s(sC, C.p + ((size_t)blk * 9 << LVB), cb, bar);
+        bulk_g2s(sS, C.sc + ((size_t)blk << LVB), sb, bar);
+    }
+
+    int lc[4], cg[4];
+    local_coords(gg, l, lc);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) cg[mu] = (bc[mu] << LB) + lc[mu];
+
+    // 1. hopping part of D x from global memory while the copies land
+    Cx<float> acc[12];
+    if (!x_zero) hop_site<false>(gg, cg, i, xx, Ug, acc);
+
+    const bool ok = mbar_wait_bounded(bar, 0, WAIT_LIMIT_NS);
+    if (!__syncthreads_and(ok)) {
+        mbar_wait_bounded(bar, 0, WAIT_LIMIT_NS);
+        if (l == 0) atomicOr(status, MGC_DEV_TIMEOUT);
+        return;
+    }
+    if (HL::EXPAND) {
+        // rows 0 and 1 staged in the r area; row 2 = conj(row0 x row1) once per link
+        const uint2 *st = reinterpret_cast<const uint2 *>(rs);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            Cx<float> u[9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint2 v = st[(mu * 3 + k) * VB + l];
+                const float2 a = unpack_half2(v.x), c2 = unpack_half2(v.y);
+                u[2 * k] = {a.x, a.y};
+                u[2 * k + 1] = {c2.x, c2.y};
+            }
+            reconstruct_row2(u);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sL[(mu * 9 + k) * VB + l] = pack_half2(u[k].r, u[k].i);
+        }
+        __syncthreads();  // links complete, r area free
+    }
+    const StagedC<Clover16> Cs{sC, sS, LVB};
+
+    Cx<float> rv[12];
+    bb.load(i, rv);
+    if (!x_zero) {
+        Cx<float> xs[12], cx[12];
+        xx.load(i, xs);
+        Cs.mul(l, xs, cx);
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            rv[k] = Cx<float>{rv[k].r - fmaf(-kappa, acc[k].r, cx[k].r), rv[k].i - fmaf(-kappa, acc[k].i, cx[k].i)};
+    }
+    int nf[4], nb[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        int t[4] = {lc[0], lc[1], lc[2], lc[3]};
+        t[mu] = lc[mu] + 1;
+        nf[mu] = (t[mu] < (1 << LB)) ? local_index(gg, t) : -1;
+        t[mu] = lc[mu] - 1;
+        nb[mu] = (t[mu] >= 0) ? local_index(gg, t) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) rs[k * VB + l] = make_float4(rv[2 * k].r, rv[2 * k].i, rv[2 * k + 1].r, rv[2 * k + 1].i);
+    Cx<float> e[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) e[k] = Cx<float>{0.f, 0.f};
+    __syncthreads();
+
+    // 2. minimal residual on D_B
+    for (int it = 0; it < nmr; ++it) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = Cx<float>{0.f, 0.f};
+        if (nf[0] >= 0) h16_hop<0, -1, VB>(rs, nf[0], sL, l, acc);
+        if (nb[0] >= 0) h16_hop<0, +1, VB>(rs, nb[0], sL, nb[0], acc);
+        if (nf[1] >= 0) h16_hop<1, -1, VB>(rs, nf[1], sL, l, acc);
+        if (nb[1] >= 0) h16_hop<1, +1, VB>(rs, nb[1], sL, nb[1], acc);
+        if (nf[2] >= 0) h16_hop<2, -1, VB>(rs, nf[2], sL, l, acc);
+        if (nb[2] >= 0) h16_hop<2, +1, VB>(rs, nb[2], sL, nb[2], acc);
+        if (nf[3] >= 0) h16_hop<3, -1, VB>(rs, nf[3], sL, l, acc);
+        if (nb[3] >= 0) h16_hop<3, +1, VB>(rs, nb[3], sL, nb[3], acc);
+        Cx<float> rv2[12], p[12];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 v = rs[k * VB + l];
+            rv2[2 * k] = {v.x, v.y};
+            rv2[2 * k + 1] = {v.z, v.w};
+        }
+        Cs.mul(l, rv2, p);
+        float pr = 0.f, pi = 0.f, pp = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            p[k] = Cx<float>{fmaf(-kappa, acc[k].r, p[k].r), fmaf(-kappa, acc[k].i, p[k].i)};
+            pr = fmaf(p[k].r, rv2[k].r, fmaf(p[k].i, rv2[k].i, pr));
+            pi = fmaf(p[k].r, rv2[k].i, fmaf(-p[k].i, rv2[k].r, pi));
+            pp = fmaf(p[k].r, p[k].r, fmaf(p[k].i, p[k].i, pp));
+        }
+        block_sum3(pr, pi, pp, red);
+        const Cx<float> alpha = (pp > 0.f) ? Cx<float>{pr / pp, pi / pp} : Cx<float>{0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            e[k] = cfma(alpha, rv2[k], e[k]);
+            rv2[k] = rv2[k] - alpha * p[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            rs[k * VB + l] = make_float4(rv2[2 * k].r, rv2[2 * k].i, rv2[2 * k + 1].r, rv2[2 * k + 1].i);
+        __syncthreads();
+    }
+
+    // 3. x_B += e
+    if (!x_zero) {
+        Cx<float> xo[12];
+        xx.load(i, xo);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) e[k] = e[k] + xo[k];
+    }
+    xx.store(i, e);
+}
+
+template <int LVB, class GA>
+static int sap_run_h16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clover16 C, int nrhs, int n_cy, int n_mr,
+                       int x_is_zero, cudaStream_t s, int compress)
+{
+    const Geom &g = op->gauge->lat->g;
+    constexpr size_t smem = h16_smem_bytes<LVB>();
+    auto kern = k_sap_h16<LVB, GA>;
+    MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(g.nblocks / 2, nrhs);
+    for (int cy = 0; cy < n_cy; ++cy)
+        for (int colour = 0; colour < 2; ++colour) {
+            const int xz = (cy == 0 && colour == 0) ? x_is_zero : 0;
+            kern<<<grid, 1 << LVB, smem, s>>>(g, b, x, U, C, (float)op->kappa, colour, n_mr, xz, op->d_status);
+            count(1, sap_launch_bytes(g, 16, compress, nrhs, xz != 0));
+        }
+    MGC_CUDA(cudaGetLastError());
+    return MGC_OK;
+}
+
+// FP16 storage: the compile-time kernel for cubic 2^4 and 4^4 domains
+template <class GA>
+static int sap_dispatch16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clover16 C, int nrhs, int n_cy,
+                          int n_mr, int x_is_zero, cudaStream_t s, int compress)
+{
+    const Geom &g = op->gauge->lat->g;
+    const bool cube = g.lb[0] == g.lb[1] && g.lb[1] == g.lb[2] && g.lb[2] == g.lb[3];
+    if (cube && g.lvb == 8) return sap_run_h16<8>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, compress);
+    if (cube && g.lvb == 4) return sap_run_h16<4>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, compress);
+    return sap_run_staged(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, 16, compress);
+}
+
 // Self-test of the bounded wait used above: one block waits on an mbarrier of
 // arrival count 1; with arrive != 0 thread 0 arrives and the wait completes,
 // with arrive == 0 nothing arrives and every thread gives up after limit_ns.
@@ -598,10 +840,8 @@ int launch_sap(const mgc_clover_s *op, int prec, const void *b, void *x, int nrh
     Spinor16 X{(uint4 *)x, (float *)((uint4 *)x + nV * 3), g.lvb};
     Clover16 C{(uint4 *)op->C16, op->C16_sc, g.lvb};
     if (cp == 12)
-        return sap_run_staged(op, B, X, Gauge16x12{(uint2 *)ga->U16, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s, prec,
-                              cp);
-    return sap_run_staged(op, B, X, Gauge16x18{(uint32_t *)ga->U16, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s, prec,
-                          cp);
+        return sap_dispatch16(op, B, X, Gauge16x12{(uint2 *)ga->U16, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s, cp);
+    return sap_dispatch16(op, B, X, Gauge16x18{(uint32_t *)ga->U16, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s, cp);
 }
 
 }  // namespace mgc
