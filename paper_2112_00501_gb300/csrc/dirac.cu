@@ -185,29 +185,50 @@ int launch_gauge_pack(const Geom &g, const double *canon_dev, int prec, int comp
 }
 
 // ------------------------------------------------------------------ D, D^dagger
-template <bool DAG, class SP, class GA, class CL>
+// LVB > 0: cubic domains of 2^LVB sites, whose extents the compiler then knows
+// (shifts and masks of the index arithmetic become constants); LVB == 0: any
+// domain shape, read from g at run time.
+template <bool DAG, int LVB, class SP, class GA, class CL>
 __global__ void __launch_bounds__(256) k_dirac(Geom g, SP in, SP out, GA U, CL C, typename SP::Real kappa)
 {
     using T = typename SP::Real;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.V) return;
     const int r = blockIdx.y;
-    const SP src = shift_rhs(in, r, g.V);
+    SP src = shift_rhs(in, r, g.V), dst = shift_rhs(out, r, g.V);
+    GA Ug = U;
+    CL Cg = C;
+    Geom gg = g;
+    if (LVB > 0) {
+        gg.lvb = LVB;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) gg.lb[mu] = LVB / 4;
+        src.lvb = dst.lvb = Ug.lvb = Cg.lvb = LVB;
+    }
     int c[4];
-    site_coords(g, i, c);
+    site_coords(gg, i, c);
     Cx<T> o[12];
-    dirac_site<DAG>(g, c, i, src, U, C, kappa, o);
-    shift_rhs(out, r, g.V).store(i, o);
+    dirac_site<DAG>(gg, c, i, src, Ug, Cg, kappa, o);
+    dst.store(i, o);
+}
+
+template <int LVB, class SP, class GA, class CL>
+static void dirac_launch(const Geom &g, bool dag, SP in, SP out, GA U, CL C, double kappa, int nrhs, cudaStream_t s)
+{
+    using T = typename SP::Real;
+    dim3 grid(grid_for(g.V, 256), nrhs);
+    if (dag) k_dirac<true, LVB><<<grid, 256, 0, s>>>(g, in, out, U, C, (T)kappa);
+    else k_dirac<false, LVB><<<grid, 256, 0, s>>>(g, in, out, U, C, (T)kappa);
 }
 
 template <class SP, class GA, class CL>
 static void dirac_dispatch(const Geom &g, bool dag, SP in, SP out, GA U, CL C, double kappa, int nrhs,
                            cudaStream_t s)
 {
-    using T = typename SP::Real;
-    dim3 grid(grid_for(g.V, 256), nrhs);
-    if (dag) k_dirac<true><<<grid, 256, 0, s>>>(g, in, out, U, C, (T)kappa);
-    else k_dirac<false><<<grid, 256, 0, s>>>(g, in, out, U, C, (T)kappa);
+    const bool cube = g.lb[0] == g.lb[1] && g.lb[1] == g.lb[2] && g.lb[2] == g.lb[3];
+    if (cube && g.lvb == 8) dirac_launch<8>(g, dag, in, out, U, C, kappa, nrhs, s);
+    else if (cube && g.lvb == 4) dirac_launch<4>(g, dag, in, out, U, C, kappa, nrhs, s);
+    else dirac_launch<0>(g, dag, in, out, U, C, kappa, nrhs, s);
 }
 
 static Clover16 cl16(const Geom &g, const mgc_clover_s *op)

@@ -9,6 +9,29 @@
 
 namespace mgc {
 
+// h = P psi(j) for the projector 1 + SGN gamma_mu, with the t-boundary sign
+template <int MU, int SGN, class SP, typename T>
+__device__ __forceinline__ void load_project(const SP &in, int j, bool flip, Cx<T> h[6])
+{
+    Cx<T> s[12];
+    in.load(j, s);
+    project<MU, SGN>(s, h);
+    if (flip) negate6(h);
+}
+
+// FP16 spinors: project the stored halves and apply the per-site scale (and
+// the boundary sign) to the six projected components only
+template <int MU, int SGN>
+__device__ __forceinline__ void load_project(const Spinor16 &in, int j, bool flip, Cx<float> h[6])
+{
+    Cx<float> s[12];
+    in.load_raw(j, s);
+    project<MU, SGN>(s, h);
+    const float sc = flip ? -in.scale_of(j) : in.scale_of(j);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h[k] = sc * h[k];
+}
+
 template <int MU, bool DAG, class SP, class GA, typename T>
 __device__ __forceinline__ void hop_dir(const Geom &g, const int c[4], int i, const SP &in, const GA &U,
                                         Cx<T> acc[12])
@@ -16,19 +39,15 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const int c[4], int i, co
     constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF gamma_mu
     constexpr int SB = -SF;            // backward projector 1 + SB gamma_mu
     bool wr;
-    Cx<T> s[12], h[6], w[6], u[9];
+    Cx<T> h[6], w[6], u[9];
     int j = neighbour(g, c, MU, +1, &wr);
-    in.load(j, s);
-    project<MU, SF>(s, h);
-    if (MU == 3 && wr && g.tbc < 0) negate6(h);
+    load_project<MU, SF>(in, j, MU == 3 && wr && g.tbc < 0, h);
     U.load(i, MU, u);
     su3_mul(u, h, w);
     reconstruct_add<MU, SF>(acc, w);
 
     j = neighbour(g, c, MU, -1, &wr);
-    in.load(j, s);
-    project<MU, SB>(s, h);
-    if (MU == 3 && wr && g.tbc < 0) negate6(h);
+    load_project<MU, SB>(in, j, MU == 3 && wr && g.tbc < 0, h);
     U.load(j, MU, u);
     su3_dag_mul(u, h, w);
     reconstruct_add<MU, SB>(acc, w);
@@ -46,6 +65,25 @@ __device__ __forceinline__ void hop_site(const Geom &g, const int c[4], int i, c
     hop_dir<3, DAG>(g, c, i, in, U, acc);
 }
 
+// out = C(i) psi
+template <class CL, typename T>
+__device__ __forceinline__ void clover_site(const CL &C, int i, const Cx<T> psi[12], Cx<T> out[12])
+{
+    T cl[72];
+    C.load(i, cl);
+    clover_mul(cl, psi, out);
+}
+
+// FP16 clover: multiply with the stored halves, scale the twelve results
+__device__ __forceinline__ void clover_site(const Clover16 &C, int i, const Cx<float> psi[12], Cx<float> out[12])
+{
+    float cl[72];
+    const float sc = C.load_raw(i, cl);
+    clover_mul(cl, psi, out);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = sc * out[k];
+}
+
 // (D psi)(x) = C(x) psi(x) - kappa * hop  at packed site i with coordinates c
 template <bool DAG, class SP, class GA, class CL, typename T>
 __device__ __forceinline__ void dirac_site(const Geom &g, const int c[4], int i, const SP &in, const GA &U,
@@ -54,9 +92,7 @@ __device__ __forceinline__ void dirac_site(const Geom &g, const int c[4], int i,
     Cx<T> acc[12], psi[12];
     hop_site<DAG>(g, c, i, in, U, acc);
     in.load(i, psi);
-    T cl[72];
-    C.load(i, cl);
-    clover_mul(cl, psi, out);
+    clover_site(C, i, psi, out);
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[k] = Cx<T>{fma(-kappa, acc[k].r, out[k].r), fma(-kappa, acc[k].i, out[k].i)};
 }

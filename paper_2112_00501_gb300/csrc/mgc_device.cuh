@@ -223,6 +223,21 @@ struct Spinor16 {
     {
         return p + ((size_t)(i >> lvb) * 3 << lvb) + (i & ((1 << lvb) - 1));
     }
+    // the stored halves without the scale, and the scale
+    __device__ __forceinline__ void load_raw(int i, Cx<float> s[12]) const
+    {
+        const uint4 *q = at(i);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 v = __ldg(q + ((size_t)k << lvb));
+            float2 a = unpack_half2(v.x), b = unpack_half2(v.y), c = unpack_half2(v.z), d = unpack_half2(v.w);
+            s[4 * k + 0] = {a.x, a.y};
+            s[4 * k + 1] = {b.x, b.y};
+            s[4 * k + 2] = {c.x, c.y};
+            s[4 * k + 3] = {d.x, d.y};
+        }
+    }
+    __device__ __forceinline__ float scale_of(int i) const { return __ldg(sc + i); }
     __device__ __forceinline__ void load(int i, Cx<float> s[12]) const
     {
         const uint4 *q = at(i);
@@ -413,6 +428,25 @@ struct Clover16 {
     float *sc;
     int lvb;
     using Real = float;
+    // the stored halves without the scale, and the scale
+    __device__ __forceinline__ float load_raw(int i, float c[72]) const
+    {
+        const uint4 *q = p + ((size_t)(i >> lvb) * 9 << lvb) + (i & ((1 << lvb) - 1));
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            uint4 v = __ldg(q + ((size_t)k << lvb));
+            float2 a = unpack_half2(v.x), b = unpack_half2(v.y), cc = unpack_half2(v.z), d = unpack_half2(v.w);
+            c[8 * k + 0] = a.x;
+            c[8 * k + 1] = a.y;
+            c[8 * k + 2] = b.x;
+            c[8 * k + 3] = b.y;
+            c[8 * k + 4] = cc.x;
+            c[8 * k + 5] = cc.y;
+            c[8 * k + 6] = d.x;
+            c[8 * k + 7] = d.y;
+        }
+        return __ldg(sc + i);
+    }
     __device__ __forceinline__ void load(int i, float c[72]) const
     {
         const uint4 *q = p + ((size_t)(i >> lvb) * 9 << lvb) + (i & ((1 << lvb) - 1));
