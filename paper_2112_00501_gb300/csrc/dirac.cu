@@ -189,7 +189,8 @@ int launch_gauge_pack(const Geom &g, const double *canon_dev, int prec, int comp
 // (shifts and masks of the index arithmetic become constants); LVB == 0: any
 // domain shape, read from g at run time.
 template <bool DAG, int LVB, class SP, class GA, class CL>
-__global__ void __launch_bounds__(256) k_dirac(Geom g, SP in, SP out, GA U, CL C, typename SP::Real kappa)
+__global__ void __launch_bounds__(256, (LVB > 0 && sizeof(typename SP::Real) == 4) ? 3 : 1)
+    k_dirac(Geom g, SP in, SP out, GA U, CL C, typename SP::Real kappa)
 {
     using T = typename SP::Real;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
