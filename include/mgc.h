@@ -261,6 +261,65 @@ int mgc_solve_noalloc(mgc_clover_t op, const double *b, double *x, const mgc_sol
 int mgc_force(mgc_clover_t op, const double *phi, double *dSdU, const mgc_solve_params *p,
               mgc_solve_info *info, double *action, void *stream);
 
+/*
+ * Batches of lattices (no paper counterpart; the paper's multiple
+ * right-hand sides, Sec. 4, extended to several lattices at once).  A batch
+ * groups up to MGC_BATCH_MAX operators that share storage precision, link
+ * compression and SAP domain shape; operator k carries nrhs[k] >= 1
+ * right-hand sides.  One kernel launch then covers every lattice and every
+ * right-hand side: the batched D applies one launch per call, the batched
+ * smoother one launch per colour and sweep, replayed from a CUDA graph
+ * captured on first use.  An autotuner times the launch shapes (right-hand
+ * sides per thread, threads per block, order of the thread blocks) on first
+ * use at each precision and keeps the fastest.  The batch does not own the
+ * operators: destroy it before them.
+ *
+ * Fields passed to the batch functions are arrays of n pointers, one per
+ * operator, each to nrhs[k] packed (apply, smoother) or canonical (solve)
+ * fields back to back.
+ */
+#define MGC_BATCH_MAX 8
+typedef struct mgc_batch_s *mgc_batch_t;
+int mgc_batch_create(const mgc_clover_t *ops, const int *nrhs, int n, mgc_batch_t *out);
+int mgc_batch_destroy(mgc_batch_t b);
+/* total right-hand sides (systems) of the batch */
+int mgc_batch_systems(mgc_batch_t b);
+/* out_k = D in_k (dagger = 0) or D^dagger in_k for every operator k; prec as in mgc_apply_D */
+int mgc_batch_apply_D(mgc_batch_t b, const void *const *in, void *const *out, int prec, int dagger, void *stream);
+/*
+ * mgc_sap_smooth on every operator of the batch (prec 32 or 16).  The 2 n_cy
+ * launches are captured once into a CUDA graph per distinct argument set
+ * (pointers, n_cy, n_mr, prec, x_is_zero; the last few are kept) and replayed.
+ */
+int mgc_batch_sap_smooth(mgc_batch_t b, const void *const *rhs, void *const *x, int n_cy, int n_mr, int prec,
+                         int x_is_zero, void *stream);
+/*
+ * Solve D_k x = b for every right-hand side of every operator with the
+ * two-level method (p->method must be 2, p->precond 1): FP64 defect
+ * correction around an FP32 FGCR + SAP inner solve, all systems advancing in
+ * lock step so that each step is one launch over the whole batch.  Every
+ * system has its own Krylov coefficients, computed on the device; a system
+ * that has converged stops changing.  b, x: arrays of n canonical complex128
+ * pointers (nrhs[k] fields each; on_device as in p).  info: one entry per
+ * system, operator-major.  Returns the worst status.  Synchronises stream.
+ */
+int mgc_batch_solve(mgc_batch_t b, const double *const *rhs, double *const *x, const mgc_solve_params *p,
+                    mgc_solve_info *info, void *stream);
+/*
+ * Launch shape chosen for D at precision prec (tuning now if not yet done;
+ * force != 0 re-tunes): right-hand sides per thread, threads per block and
+ * whether thread blocks of one site block and different right-hand sides are
+ * adjacent; and for the smoother the same block order flag.
+ */
+int mgc_batch_tune(mgc_batch_t b, int prec, int force, int *rhs_per_thread, int *threads, int *rhs_fast_d,
+                   int *rhs_fast_sap, void *stream);
+/*
+ * Pin the launch shape at precision prec instead of tuning: rhs_per_thread
+ * 1, 2 or 4; threads 128 or 256; rhs_fast_d, rhs_fast_sap 0 or 1.
+ */
+int mgc_batch_set_shape(mgc_batch_t b, int prec, int rhs_per_thread, int threads, int rhs_fast_d,
+                        int rhs_fast_sap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,23 @@ def _c(a):
     return np.ascontiguousarray(a, dtype=np.complex128)
 
 
+def _sized(a, n, what):
+    """a as contiguous complex128, refusing any size but n entries: the C
+    routines index whole-lattice arrays without knowing their length."""
+    a = _c(a)
+    if a.size != n:
+        raise ValueError(f"{what}: expected {n} complex entries, got {a.size} (shape {a.shape})")
+    return a
+
+
+def _vol(dims):
+    return int(np.prod([int(d) for d in dims]))
+
+
+def _vb(bdims):
+    return int(np.prod([int(b) for b in bdims]))
+
+
 def threads() -> int:
     """Number of OpenMP threads the oracle uses (1 without OpenMP)."""
     return int(lib().or_threads())
@@ -88,13 +105,17 @@ def sigma():
 def field_strength_site(dims, U, site):
     """F_{mu nu}(x) for the planes (01, 02, 03, 12, 13, 23), shape (6, 3, 3)."""
     out = np.zeros((6, 3, 3), np.complex128)
-    lib().or_field_strength_site(_dims(dims), _c(U), int(site), out)
+    if not 0 <= int(site) < _vol(dims):
+        raise ValueError("site out of range")
+    lib().or_field_strength_site(_dims(dims), _sized(U, _vol(dims) * 36, "U"), int(site), out)
     return out
 
 
 def clover_site(dims, kappa, csw, U, site):
     out = np.zeros((12, 12), np.complex128)
-    lib().or_clover_site(_dims(dims), float(kappa), float(csw), _c(U), int(site), out)
+    if not 0 <= int(site) < _vol(dims):
+        raise ValueError("site out of range")
+    lib().or_clover_site(_dims(dims), float(kappa), float(csw), _sized(U, _vol(dims) * 36, "U"), int(site), out)
     return out
 
 
@@ -102,7 +123,7 @@ def clover(dims, kappa, csw, U):
     """C(x) = 1 + i kappa c_SW sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x), (V, 12, 12)."""
     V = int(np.prod(dims))
     out = np.zeros((V, 12, 12), np.complex128)
-    lib().or_clover_build(_dims(dims), float(kappa), float(csw), _c(U), out)
+    lib().or_clover_build(_dims(dims), float(kappa), float(csw), _sized(U, V * 36, "U"), out)
     return out
 
 
@@ -116,25 +137,32 @@ def invert(A):
 
 
 def clover_inverse(dims, Cl):
-    out = np.zeros_like(_c(Cl))
-    if lib().or_clover_invert(_dims(dims), _c(Cl), out) != 0:
+    Cl = _sized(Cl, _vol(dims) * 144, "Cl")
+    out = np.zeros_like(Cl)
+    if lib().or_clover_invert(_dims(dims), Cl, out) != 0:
         raise ZeroDivisionError("singular clover block")
     return out
 
 
 def dirac(dims, tbc, kappa, U, Cl, psi, dagger=False):
     """D psi (or D^dagger psi) on the whole lattice; psi (V, 4, 3)."""
-    psi = _c(psi)
+    V = _vol(dims)
+    psi = _sized(psi, V * 12, "psi")
     out = np.zeros_like(psi)
-    lib().or_dirac(_dims(dims), int(tbc), float(kappa), _c(U), _c(Cl), psi, out, int(bool(dagger)))
+    lib().or_dirac(_dims(dims), int(tbc), float(kappa), _sized(U, V * 36, "U"), _sized(Cl, V * 144, "Cl"), psi,
+                   out, int(bool(dagger)))
     return out
 
 
 def dirac_at(dims, tbc, kappa, csw, U, psi, sites, dagger=False):
     """D psi at the listed sites only (clover built on the fly); (n, 4, 3)."""
-    sites = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
+    V = _vol(dims)
+    sites = np.ascontiguousarray(np.asarray(sites, dtype=np.int64).reshape(-1))
+    if sites.size and (sites.min() < 0 or sites.max() >= V):
+        raise ValueError("site out of range")
     out = np.zeros((len(sites), 4, 3), np.complex128)
-    lib().or_dirac_at(_dims(dims), int(tbc), float(kappa), float(csw), _c(U), _c(psi),
+    lib().or_dirac_at(_dims(dims), int(tbc), float(kappa), float(csw), _sized(U, V * 36, "U"),
+                      _sized(psi, V * 12, "psi"),
                       len(sites), sites, out, int(bool(dagger)))
     return out
 
@@ -155,37 +183,44 @@ def block_sites(dims, bdims, bc):
 
 def dirac_block(dims, bdims, bc, kappa, U, Cl, v, dagger=False):
     """Dirichlet block operator D_B on a block vector v (V_B, 4, 3)."""
-    v = _c(v)
+    V = _vol(dims)
+    v = _sized(v, _vb(bdims) * 12, "v")
     out = np.zeros_like(v)
-    lib().or_dirac_block(_dims(dims), _dims(bdims), _dims(bc), float(kappa), _c(U), _c(Cl), v,
+    lib().or_dirac_block(_dims(dims), _dims(bdims), _dims(bc), float(kappa), _sized(U, V * 36, "U"),
+                         _sized(Cl, V * 144, "Cl"), v,
                          out, int(bool(dagger)))
     return out
 
 
 def mr_block(dims, bdims, bc, kappa, U, Cl, r, nmr, return_residual=False):
     """k = nmr minimal-residual steps on D_B e = r from e = 0."""
-    r = _c(r)
+    V = _vol(dims)
+    r = _sized(r, _vb(bdims) * 12, "r")
     e = np.zeros_like(r)
     rout = np.zeros_like(r) if return_residual else None
-    lib().or_mr_block(_dims(dims), _dims(bdims), _dims(bc), float(kappa), _c(U), _c(Cl), r, e,
+    lib().or_mr_block(_dims(dims), _dims(bdims), _dims(bc), float(kappa), _sized(U, V * 36, "U"),
+                      _sized(Cl, V * 144, "Cl"), r, e,
                       None if rout is None else rout.ctypes.data, int(nmr))
     return (e, rout) if return_residual else e
 
 
 def mr_block_at(dims, bdims, bc, kappa, csw, U, r, nmr):
     """MR on one block with its clover built on the fly (no full clover field)."""
-    r = _c(r)
+    r = _sized(r, _vb(bdims) * 12, "r")
     e = np.zeros_like(r)
-    lib().or_mr_block_at(_dims(dims), _dims(bdims), _dims(bc), float(kappa), float(csw), _c(U), r, e,
+    lib().or_mr_block_at(_dims(dims), _dims(bdims), _dims(bc), float(kappa), float(csw),
+                         _sized(U, _vol(dims) * 36, "U"), r, e,
                          int(nmr))
     return e
 
 
 def sap(dims, bdims, tbc, kappa, U, Cl, b, x0=None, ncy=4, nmr=4):
     """n_cy multiplicative SAP sweeps on D x = b; returns the updated x."""
-    b = _c(b)
-    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128, copy=True)
-    lib().or_sap(_dims(dims), _dims(bdims), int(tbc), float(kappa), _c(U), _c(Cl), b, x,
+    V = _vol(dims)
+    b = _sized(b, V * 12, "b")
+    x = np.zeros_like(b) if x0 is None else _sized(np.array(x0, dtype=np.complex128, copy=True), V * 12, "x0")
+    lib().or_sap(_dims(dims), _dims(bdims), int(tbc), float(kappa), _sized(U, V * 36, "U"), _sized(Cl, V * 144, "Cl"),
+                 b, x,
                  int(ncy), int(nmr))
     return x
 
@@ -193,11 +228,13 @@ def sap(dims, bdims, tbc, kappa, U, Cl, b, x0=None, ncy=4, nmr=4):
 def solve(dims, bdims, tbc, kappa, U, Cl, b, method="fgcr", precond="sap", ncy=4, nmr=4,
           m=16, tol=1e-10, max_iter=1000, x0=None):
     """Solve D x = b.  Returns (x, status, iterations, true relative residual)."""
-    b = _c(b)
-    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128, copy=True)
+    V = _vol(dims)
+    b = _sized(b, V * 12, "b")
+    x = np.zeros_like(b) if x0 is None else _sized(np.array(x0, dtype=np.complex128, copy=True), V * 12, "x0")
     it = C.c_int(0)
     res = C.c_double(0)
-    st = lib().or_solve(_dims(dims), _dims(bdims), int(tbc), float(kappa), _c(U), _c(Cl), b, x,
+    st = lib().or_solve(_dims(dims), _dims(bdims), int(tbc), float(kappa), _sized(U, V * 36, "U"),
+                        _sized(Cl, V * 144, "Cl"), b, x,
                         {"fgcr": 0, "fbicgstab": 1}[method], {"none": 0, "sap": 1}[precond],
                         int(ncy), int(nmr), int(m), float(tol), int(max_iter), C.byref(it),
                         C.byref(res))
@@ -215,7 +252,8 @@ def force(dims, tbc, kappa, csw, U, X, Y):
     """dS/dRe U + i dS/dIm U for S = ||Y||^2, Y = D^-dagger phi, X = D^-1 Y."""
     V = int(np.prod(dims))
     g = np.zeros((V, 4, 3, 3), np.complex128)
-    lib().or_force(_dims(dims), int(tbc), float(kappa), float(csw), _c(U), _c(X), _c(Y), g)
+    lib().or_force(_dims(dims), int(tbc), float(kappa), float(csw), _sized(U, V * 36, "U"), _sized(X, V * 12, "X"),
+                   _sized(Y, V * 12, "Y"), g)
     return g
 
 

@@ -78,7 +78,18 @@ SIGNATURES = {
     "mgc_solve": (_I, [_P, _P, _P, _I, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P]),
     "mgc_force": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(SolveInfo), C.POINTER(_D), _P]),
     "mgc_solve_noalloc": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P]),
+    "mgc_batch_create": (_I, [C.POINTER(_P), C.POINTER(_I), _I, C.POINTER(_P)]),
+    "mgc_batch_destroy": (_I, [_P]),
+    "mgc_batch_systems": (_I, [_P]),
+    "mgc_batch_apply_D": (_I, [_P, C.POINTER(_P), C.POINTER(_P), _I, _I, _P]),
+    "mgc_batch_sap_smooth": (_I, [_P, C.POINTER(_P), C.POINTER(_P), _I, _I, _I, _I, _P]),
+    "mgc_batch_solve": (_I, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(SolveParams), C.POINTER(SolveInfo),
+                             _P]),
+    "mgc_batch_tune": (_I, [_P, _I, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), _P]),
+    "mgc_batch_set_shape": (_I, [_P, _I, _I, _I, _I, _I]),
 }
+
+MGC_BATCH_MAX = 8
 
 _lib = None
 

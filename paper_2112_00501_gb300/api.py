@@ -244,3 +244,94 @@ class CloverOperator:
         check(self.lib.mgc_force(self.handle, _ptr(ph), _ptr(g), C.byref(p), C.byref(info), C.byref(S),
                                  _stream(stream)), "mgc_force")
         return g, float(S.value), info
+
+
+def _ptr_array(ts):
+    return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+class Batch:
+    """Several operators (same storage format and SAP domain shape) with nrhs[k]
+    right-hand sides each, driven by one launch per step (the ABI's mgc_batch_t).
+    Field arguments are lists with one tensor per operator."""
+
+    def __init__(self, ops, nrhs):
+        if len(ops) != len(nrhs) or not 1 <= len(ops) <= _lib.MGC_BATCH_MAX:
+            raise ValueError(f"need 1..{_lib.MGC_BATCH_MAX} operators, one nrhs each")
+        self.lib = ops[0].lib
+        self.ops = list(ops)
+        self.nrhs = [int(n) for n in nrhs]
+        h = C.c_void_p()
+        hs = (C.c_void_p * len(ops))(*[op.handle.value for op in ops])
+        nr = (C.c_int * len(ops))(*self.nrhs)
+        check(self.lib.mgc_batch_create(hs, nr, len(ops), C.byref(h)), "mgc_batch_create")
+        self.handle = h
+        self.systems = int(self.lib.mgc_batch_systems(h))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self.lib.mgc_batch_destroy(h)
+            self.handle = None
+
+    def empty_packed(self, prec: int):
+        return [op.lattice.empty_packed(prec, n) for op, n in zip(self.ops, self.nrhs)]
+
+    def zeros_packed(self, prec: int):
+        return [op.lattice.zeros_packed(prec, n) for op, n in zip(self.ops, self.nrhs)]
+
+    def apply_D(self, xs, prec: int, dagger=False, out=None, stream=None):
+        out = self.empty_packed(prec) if out is None else out
+        check(self.lib.mgc_batch_apply_D(self.handle, _ptr_array(xs), _ptr_array(out), prec, int(bool(dagger)),
+                                         _stream(stream)), "mgc_batch_apply_D")
+        return out
+
+    def sap_smooth(self, bs, xs, prec: int, n_cy: int = 4, n_mr: int = 4, x_is_zero=False, stream=None):
+        check(self.lib.mgc_batch_sap_smooth(self.handle, _ptr_array(bs), _ptr_array(xs), n_cy, n_mr, prec,
+                                            int(bool(x_is_zero)), _stream(stream)), "mgc_batch_sap_smooth")
+        return xs
+
+    def tune(self, prec: int, force=False, stream=None) -> dict:
+        v = [C.c_int(0) for _ in range(4)]
+        check(self.lib.mgc_batch_tune(self.handle, prec, int(bool(force)), *[C.byref(x) for x in v],
+                                      _stream(stream)), "mgc_batch_tune")
+        return {"rhs_per_thread": v[0].value, "threads": v[1].value, "rhs_fast_d": v[2].value,
+                "rhs_fast_sap": v[3].value}
+
+    def set_shape(self, prec: int, rhs_per_thread: int, threads: int, rhs_fast_d: int, rhs_fast_sap: int):
+        check(self.lib.mgc_batch_set_shape(self.handle, prec, rhs_per_thread, threads, rhs_fast_d, rhs_fast_sap),
+              "mgc_batch_set_shape")
+
+    def solve(self, bs, params: SolveParams | None = None, x0=None, out=None, stream=None, **kw):
+        """Solve every system; bs[k]: canonical (nrhs[k], V, 4, 3) complex128, all on
+        the GPU or all on the host (pinned).  Returns (xs, infos) with one info per
+        system, operator-major."""
+        p = params if params is not None else solve_params(**kw)
+        host = not (isinstance(bs[0], torch.Tensor) and bs[0].is_cuda)
+        dev = "cpu" if host else "cuda"
+        bt = []
+        for b, op, n in zip(bs, self.ops, self.nrhs):
+            t = _canon(b, dev).reshape(n, op.lattice.volume, 4, 3)
+            if host and not t.is_pinned():
+                t = t.pin_memory()
+            bt.append(t)
+        p.on_device = 0 if host else 1
+        if x0 is not None:
+            xs = [_canon(x, dev).reshape(t.shape).clone() for x, t in zip(x0, bt)]
+            if host:
+                xs = [x.pin_memory() for x in xs]
+            p.x_is_guess = 1
+        elif out is not None:
+            xs = list(out)
+            p.x_is_guess = 0
+        else:
+            xs = [torch.zeros_like(t) for t in bt]
+            if host:
+                xs = [x.pin_memory() for x in xs]
+            p.x_is_guess = 0
+        infos = (SolveInfo * self.systems)()
+        st = self.lib.mgc_batch_solve(self.handle, _ptr_array(bt), _ptr_array(xs), C.byref(p), infos,
+                                      _stream(stream))
+        if st not in (_lib.MGC_OK, _lib.MGC_NOT_CONVERGED):
+            check(st, "mgc_batch_solve")
+        return xs, list(infos)

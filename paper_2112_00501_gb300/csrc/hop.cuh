@@ -65,6 +65,52 @@ __device__ __forceinline__ void hop_site(const Geom &g, const int c[4], int i, c
     hop_dir<3, DAG>(g, c, i, in, U, acc);
 }
 
+// The hopping sums of RB right-hand sides at one site, each link loaded once
+// and applied to all of them; only the first nr (<= RB) are computed.
+template <int MU, bool DAG, int RB, class SP, class GA, typename T>
+__device__ __forceinline__ void hop_dir_multi(const Geom &g, const int c[4], int i, const SP (&in)[RB], int nr,
+                                              const GA &U, Cx<T> (&acc)[RB][12])
+{
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    bool wr;
+    Cx<T> h[6], w[6], u[9];
+    int j = neighbour(g, c, MU, +1, &wr);
+    bool flip = MU == 3 && wr && g.tbc < 0;
+    U.load(i, MU, u);
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+        if (q < nr) {
+            load_project<MU, SF>(in[q], j, flip, h);
+            su3_mul(u, h, w);
+            reconstruct_add<MU, SF>(acc[q], w);
+        }
+    j = neighbour(g, c, MU, -1, &wr);
+    flip = MU == 3 && wr && g.tbc < 0;
+    U.load(j, MU, u);
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+        if (q < nr) {
+            load_project<MU, SB>(in[q], j, flip, h);
+            su3_dag_mul(u, h, w);
+            reconstruct_add<MU, SB>(acc[q], w);
+        }
+}
+
+template <bool DAG, int RB, class SP, class GA, typename T>
+__device__ __forceinline__ void hop_site_multi(const Geom &g, const int c[4], int i, const SP (&in)[RB], int nr,
+                                               const GA &U, Cx<T> (&acc)[RB][12])
+{
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[q][k] = Cx<T>{0, 0};
+    hop_dir_multi<0, DAG>(g, c, i, in, nr, U, acc);
+    hop_dir_multi<1, DAG>(g, c, i, in, nr, U, acc);
+    hop_dir_multi<2, DAG>(g, c, i, in, nr, U, acc);
+    hop_dir_multi<3, DAG>(g, c, i, in, nr, U, acc);
+}
+
 // out = C(i) psi
 template <class CL, typename T>
 __device__ __forceinline__ void clover_site(const CL &C, int i, const Cx<T> psi[12], Cx<T> out[12])

@@ -126,6 +126,28 @@ int solve_noalloc(mgc_clover_s *op, const double *b, double *x, const mgc_solve_
 int solve_packed(mgc_clover_s *op, const double2 *b, double2 *x, const mgc_solve_params *p, mgc_solve_info *info,
                  cudaStream_t s);
 
+// batches (batch.cu, with kernels in dirac.cu and sap.cu): operators of the same
+// storage format and domain shape; rhs_fast orders thread blocks with the
+// right-hand sides of one site block (or domain) next to each other
+struct BatchSpec {
+    int n;
+    int rhs_fast;
+    const mgc_clover_s *ops[MGC_BATCH_MAX];
+    int nrhs[MGC_BATCH_MAX];
+};
+// D (or D^dagger) on every operator: rb right-hand sides per thread (1, 2 or 4), threads per block
+int launch_dirac_batch(const BatchSpec &spec, int prec, bool dag, const void *const *in, void *const *out, int rb,
+                       int threads, cudaStream_t s);
+int launch_sap_batch(const BatchSpec &spec, int prec, const void *const *b, void *const *x, int n_cy, int n_mr,
+                     int x_is_zero, cudaStream_t s);
+// per-system site kernels of the batched two-level solve (systems operator-major;
+// fields are flat batch vectors, lattice k at its offset): out32 = f_s * in64 with
+// f_s = scal[s] if flag[s] else 0; x64 += g_s * e32 with g_s = scal[s] if flag[s] else 0
+int launch_scale_to32_batch(const BatchSpec &spec, const size_t *off, const double2 *in, float2 *out,
+                            const double *scal, const int *flag, cudaStream_t s);
+int launch_axpy_from32_batch(const BatchSpec &spec, const size_t *off, double2 *x, const float2 *e,
+                             const double *scal, const int *flag, cudaStream_t s);
+
 // force.cu
 int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_params *p, mgc_solve_info *info,
           double *action, cudaStream_t s);

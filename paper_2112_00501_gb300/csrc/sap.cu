@@ -366,9 +366,23 @@ static size_t staged_smem(int vb)
            96 * sizeof(float) + 16;
 }
 
+// one domain solve of the staged kernel: domain jb of `colour`, right-hand side rr
+template <class SP, class GA, class CL>
+__device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, const SP &x, const GA &U, const CL &C,
+                                                float kappa, int colour, int nmr, int x_zero, int *status, int jb,
+                                                int rr);
+
 template <class SP, class GA, class CL>
 __global__ void __launch_bounds__(256, 2) k_sap_staged(Geom g, SP b, SP x, GA U, CL C, float kappa, int colour,
                                                        int nmr, int x_zero, int *status)
+{
+    sap_staged_body(g, b, x, U, C, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
+}
+
+template <class SP, class GA, class CL>
+__device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, const SP &x, const GA &U, const CL &C,
+                                                float kappa, int colour, int nmr, int x_zero, int *status, int jb,
+                                                int rr)
 {
     using SL = Staged<GA>;
     using SC = StagedC<CL>;
@@ -389,10 +403,9 @@ __global__ void __launch_bounds__(256, 2) k_sap_staged(Geom g, SP b, SP x, GA U,
     sp += 96 * sizeof(float);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sp);
 
-    const int rr = blockIdx.y;
     const SP bb = shift_rhs(b, rr, g.V);
     const SP xx = shift_rhs(x, rr, g.V);
-    int j = blockIdx.x;
+    int j = jb;
     const int half0 = g.NB[0] >> 1;
     int bc[4];
     const int m = j % half0;
@@ -550,9 +563,23 @@ __device__ __forceinline__ void h16_hop(const float4 *rs, int n, const uint32_t 
     reconstruct_add<MU, SGN>(acc, w);
 }
 
+// one domain solve of the FP16 kernel: domain jb of `colour`, right-hand side rr
+template <int LVB, class GA>
+__device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, const Spinor16 &x, const GA &U,
+                                             const Clover16 &C, float kappa, int colour, int nmr, int x_zero,
+                                             int *status, int jb, int rr);
+
 template <int LVB, class GA>
 __global__ void __launch_bounds__(1 << LVB, 2) k_sap_h16(Geom g, Spinor16 b, Spinor16 x, GA U, Clover16 C, float kappa,
                                                          int colour, int nmr, int x_zero, int *status)
+{
+    sap_h16_body<LVB>(g, b, x, U, C, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
+}
+
+template <int LVB, class GA>
+__device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, const Spinor16 &x, const GA &U,
+                                             const Clover16 &C, float kappa, int colour, int nmr, int x_zero,
+                                             int *status, int jb, int rr)
 {
     constexpr int VB = 1 << LVB;
     constexpr int LB = LVB / 4;
@@ -570,13 +597,12 @@ __global__ void __launch_bounds__(1 << LVB, 2) k_sap_h16(Geom g, Spinor16 b, Spi
     gg.lvb = LVB;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) gg.lb[mu] = LB;
-    const int rr = blockIdx.y;
     Spinor16 bb = shift_rhs(b, rr, g.V), xx = shift_rhs(x, rr, g.V);
     bb.lvb = LVB;
     xx.lvb = LVB;
     GA Ug = U;
     Ug.lvb = LVB;
-    int j = blockIdx.x;
+    int j = jb;
     const int half0 = g.NB[0] >> 1;
     int bc[4];
     const int m = j % half0;
@@ -742,6 +768,167 @@ static int sap_dispatch16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, 
     if (cube && g.lvb == 8) return sap_run_h16<8>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, compress);
     if (cube && g.lvb == 4) return sap_run_h16<4>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, compress);
     return sap_run_staged(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, 16, compress);
+}
+
+// ------------------------------------------------------------------ batches of lattices
+// One launch covers one colour of every lattice of a batch and all their
+// right-hand sides.  Thread block b belongs to the first lattice k with
+// b < end[k]; within a lattice the order of (domain, right-hand side) pairs is
+// chosen by the caller: rhs_fast = 1 puts the right-hand sides of one domain
+// next to each other (they share the domain's links and clover term in L2).
+template <class SP, class GA, class CL> struct SapBatch {
+    int n;
+    int rhs_fast;
+    int end[MGC_BATCH_MAX];
+    int nrhs[MGC_BATCH_MAX];
+    int ndom[MGC_BATCH_MAX];  // domains of one colour
+    Geom g[MGC_BATCH_MAX];
+    SP b[MGC_BATCH_MAX], x[MGC_BATCH_MAX];
+    GA U[MGC_BATCH_MAX];
+    CL C[MGC_BATCH_MAX];
+    float kappa[MGC_BATCH_MAX];
+    int *status[MGC_BATCH_MAX];
+};
+
+template <class BT>
+__device__ __forceinline__ void batch_item(const BT &B, int &k, int &jb, int &rr)
+{
+    k = 0;
+    while (k < B.n - 1 && (int)blockIdx.x >= B.end[k]) ++k;
+    const int local = blockIdx.x - (k ? B.end[k - 1] : 0);
+    if (B.rhs_fast) {
+        rr = local % B.nrhs[k];
+        jb = local / B.nrhs[k];
+    } else {
+        jb = local % B.ndom[k];
+        rr = local / B.ndom[k];
+    }
+}
+
+template <int LVB, class GA>
+__global__ void __launch_bounds__(1 << LVB, 2) k_sap_h16_batch(SapBatch<Spinor16, GA, Clover16> B, int colour, int nmr,
+                                                               int x_zero)
+{
+    int k, jb, rr;
+    batch_item(B, k, jb, rr);
+    sap_h16_body<LVB>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
+}
+
+template <class SP, class GA, class CL>
+__global__ void __launch_bounds__(256, 2) k_sap_staged_batch(SapBatch<SP, GA, CL> B, int colour, int nmr, int x_zero)
+{
+    int k, jb, rr;
+    batch_item(B, k, jb, rr);
+    sap_staged_body(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
+}
+
+template <class SP, class GA, class CL>
+static void fill_batch(SapBatch<SP, GA, CL> &B, const BatchSpec &spec)
+{
+    B.n = spec.n;
+    B.rhs_fast = spec.rhs_fast;
+    int acc = 0;
+    for (int k = 0; k < spec.n; ++k) {
+        const mgc_clover_s *op = spec.ops[k];
+        const Geom &g = op->gauge->lat->g;
+        B.g[k] = g;
+        B.nrhs[k] = spec.nrhs[k];
+        B.ndom[k] = g.nblocks / 2;
+        acc += B.ndom[k] * spec.nrhs[k];
+        B.end[k] = acc;
+        B.kappa[k] = (float)op->kappa;
+        B.status[k] = op->d_status;
+    }
+}
+
+static Spinor16 batch_sp16(const Geom &g, const void *p, int nrhs)
+{
+    uint4 *d = (uint4 *)p;
+    return Spinor16{d, (float *)(d + (size_t)nrhs * g.V * 3), g.lvb};
+}
+
+int launch_sap_batch(const BatchSpec &spec, int prec, const void *const *b, void *const *x, int n_cy, int n_mr,
+                     int x_is_zero, cudaStream_t s)
+{
+    const mgc_clover_s *op0 = spec.ops[0];
+    const mgc_gauge_s *ga0 = op0->gauge;
+    const Geom &g0 = ga0->lat->g;
+    const int vb = 1 << g0.lvb;
+    const bool cube = g0.lb[0] == g0.lb[1] && g0.lb[1] == g0.lb[2] && g0.lb[2] == g0.lb[3];
+    int blocks = 0;
+    double bytes_x0 = 0, bytes = 0;
+    for (int k = 0; k < spec.n; ++k) {
+        const Geom &g = spec.ops[k]->gauge->lat->g;
+        blocks += g.nblocks / 2 * spec.nrhs[k];
+        bytes_x0 += sap_launch_bytes(g, prec, ga0->compress, spec.nrhs[k], true);
+        bytes += sap_launch_bytes(g, prec, ga0->compress, spec.nrhs[k], false);
+    }
+    auto run = [&](auto kern, auto &B, size_t smem) -> int {
+        MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        for (int cy = 0; cy < n_cy; ++cy)
+            for (int colour = 0; colour < 2; ++colour) {
+                const int xz = (cy == 0 && colour == 0) ? x_is_zero : 0;
+                kern<<<blocks, vb, smem, s>>>(B, colour, n_mr, xz);
+                count(1, xz ? bytes_x0 : bytes);
+            }
+        MGC_CUDA(cudaGetLastError());
+        return MGC_OK;
+    };
+    if (prec == 16) {
+        if (ga0->compress == 12) {
+            SapBatch<Spinor16, Gauge16x12, Clover16> B;
+            fill_batch(B, spec);
+            for (int k = 0; k < spec.n; ++k) {
+                const mgc_clover_s *op = spec.ops[k];
+                const Geom &g = op->gauge->lat->g;
+                B.b[k] = batch_sp16(g, b[k], spec.nrhs[k]);
+                B.x[k] = batch_sp16(g, x[k], spec.nrhs[k]);
+                B.U[k] = Gauge16x12{(uint2 *)op->gauge->U16, g.lvb};
+                B.C[k] = Clover16{(uint4 *)op->C16, op->C16_sc, g.lvb};
+            }
+            if (cube && g0.lvb == 8) return run(k_sap_h16_batch<8, Gauge16x12>, B, h16_smem_bytes<8>());
+            if (cube && g0.lvb == 4) return run(k_sap_h16_batch<4, Gauge16x12>, B, h16_smem_bytes<4>());
+            return run(k_sap_staged_batch<Spinor16, Gauge16x12, Clover16>, B, staged_smem<Gauge16x12, Clover16>(vb));
+        }
+        SapBatch<Spinor16, Gauge16x18, Clover16> B;
+        fill_batch(B, spec);
+        for (int k = 0; k < spec.n; ++k) {
+            const mgc_clover_s *op = spec.ops[k];
+            const Geom &g = op->gauge->lat->g;
+            B.b[k] = batch_sp16(g, b[k], spec.nrhs[k]);
+            B.x[k] = batch_sp16(g, x[k], spec.nrhs[k]);
+            B.U[k] = Gauge16x18{(uint32_t *)op->gauge->U16, g.lvb};
+            B.C[k] = Clover16{(uint4 *)op->C16, op->C16_sc, g.lvb};
+        }
+        if (cube && g0.lvb == 8) return run(k_sap_h16_batch<8, Gauge16x18>, B, h16_smem_bytes<8>());
+        if (cube && g0.lvb == 4) return run(k_sap_h16_batch<4, Gauge16x18>, B, h16_smem_bytes<4>());
+        return run(k_sap_staged_batch<Spinor16, Gauge16x18, Clover16>, B, staged_smem<Gauge16x18, Clover16>(vb));
+    }
+    if (prec != 32) return fail(MGC_ERR_INVALID_ARG, "batched smoother precision must be 32 or 16");
+    if (ga0->compress == 12) {
+        SapBatch<Spinor32, Gauge32x12, Clover32> B;
+        fill_batch(B, spec);
+        for (int k = 0; k < spec.n; ++k) {
+            const mgc_clover_s *op = spec.ops[k];
+            const Geom &g = op->gauge->lat->g;
+            B.b[k] = Spinor32{(float4 *)b[k], g.lvb};
+            B.x[k] = Spinor32{(float4 *)x[k], g.lvb};
+            B.U[k] = Gauge32x12{(float4 *)op->gauge->U32, g.lvb};
+            B.C[k] = Clover32{(float4 *)op->C32, g.lvb};
+        }
+        return run(k_sap_staged_batch<Spinor32, Gauge32x12, Clover32>, B, staged_smem<Gauge32x12, Clover32>(vb));
+    }
+    SapBatch<Spinor32, Gauge32x18, Clover32> B;
+    fill_batch(B, spec);
+    for (int k = 0; k < spec.n; ++k) {
+        const mgc_clover_s *op = spec.ops[k];
+        const Geom &g = op->gauge->lat->g;
+        B.b[k] = Spinor32{(float4 *)b[k], g.lvb};
+        B.x[k] = Spinor32{(float4 *)x[k], g.lvb};
+        B.U[k] = Gauge32x18{(float2 *)op->gauge->U32, g.lvb};
+        B.C[k] = Clover32{(float4 *)op->C32, g.lvb};
+    }
+    return run(k_sap_staged_batch<Spinor32, Gauge32x18, Clover32>, B, staged_smem<Gauge32x18, Clover32>(vb));
 }
 
 // Self-test of the bounded wait used above: one block waits on an mbarrier of
