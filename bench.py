@@ -186,6 +186,146 @@ BYTES_PER_SITE_ITER_DEFAULT = 7000.0
 
 
 # ---------------------------------------------------------------------- GPU side
+# batched workload: several lattices and right-hand sides in one launch per step
+BATCH_WORKLOAD = dict(lattices=[((24, 24, 24, 48), 12), ((16, 16, 16, 16), 8), ((8, 8, 8, 8), 8)],
+                      block=(4, 4, 4, 4), eps=0.4, kappa=0.1355, csw=1.0, config_index=3, prec=32, compress=18,
+                      n_cy=4, n_mr=4, restart=16, tol=1e-10, inner_tol=2e-6)
+# link force workload
+FORCE_WORKLOAD = dict(dims=(24, 24, 24, 48), block=(4, 4, 4, 4), eps=0.4, kappa=0.1355, csw=1.0, config_index=4,
+                      prec=32, compress=18)
+
+
+def bench_batch(lib, stream):
+    """The batched workload: batched D and smoother against one launch per
+    lattice, and the lock-step batched solve of all systems against solving
+    them one after another."""
+    import torch
+
+    from paper_2112_00501_gb300 import api, synth
+
+    bw = BATCH_WORKLOAD
+    ops, bs, nrhs = [], [], []
+    for dims, nr in bw["lattices"]:
+        U = synth.gauge_field(dims, bw["eps"], synth.gauge_seed(bw["config_index"]))
+        lat = api.Lattice(dims, bw["block"], -1)
+        g = api.Gauge(lat, torch.from_numpy(U).cuda(), storage_prec=bw["prec"], compress=bw["compress"])
+        ops.append(api.CloverOperator(g, bw["kappa"], bw["csw"]))
+        bs.append(torch.from_numpy(synth.gaussian_spinor(dims, synth.source_seed(bw["config_index"]),
+                                                         nrhs=nr)).cuda())
+        nrhs.append(nr)
+    B = api.Batch(ops, nrhs)
+    out = {"workload": " + ".join(f"{nr} RHS on {'x'.join(map(str, d))}" for d, nr in bw["lattices"]) +
+           f", eps={bw['eps']}, kappa={bw['kappa']}, c_sw={bw['csw']}, FP32 storage, FP32 smoother "
+           f"({bw['n_cy']} sweeps x {bw['n_mr']} MR, 4^4 domains) inside FP64 defect correction, "
+           f"tol {bw['tol']:g}"}
+    prec = bw["prec"]
+    out["shape_d"] = B.tune(prec)
+    xs = [op.lattice.pack(b, prec) for op, b in zip(ops, bs)]
+    ys = B.empty_packed(prec)
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        counters(lib, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        nl, nb = counters(lib, reset=True)
+        return e0.elapsed_time(e1) / 1e3 / n, nb / n, nl / n
+
+    t, nb, nl = timed(lambda: B.apply_D(xs, prec, out=ys), 20)
+    t1, nb1, nl1 = timed(lambda: [op.apply_D(x, prec, nr, y) for op, x, nr, y in zip(ops, xs, nrhs, ys)], 20)
+    out["dslash_batched"] = {"us": 1e6 * t, "gbs": nb / t / 1e9, "launches": nl}
+    out["dslash_per_lattice"] = {"us": 1e6 * t1, "gbs": nb1 / t1 / 1e9, "launches": nl1}
+    zs = B.zeros_packed(prec)
+    t, nb, nl = timed(lambda: B.sap_smooth(xs, zs, prec, bw["n_cy"], bw["n_mr"], x_is_zero=False), 5)
+    t1, nb1, nl1 = timed(lambda: [op.sap_smooth(x, z, prec, nr, bw["n_cy"], bw["n_mr"])
+                                  for op, x, z, nr in zip(ops, xs, zs, nrhs)], 5)
+    out["sap_batched_graph"] = {"us": 1e6 * t, "gbs": nb / t / 1e9, "launches": nl}
+    out["sap_per_lattice"] = {"us": 1e6 * t1, "gbs": nb1 / t1 / 1e9, "launches": nl1}
+    params = api.solve_params(method=2, precond=1, smoother_prec=prec, n_cy=bw["n_cy"], n_mr=bw["n_mr"],
+                              restart=bw["restart"], tol=bw["tol"], max_iter=500, inner_tol=bw["inner_tol"])
+    xsol = [torch.empty_like(b) for b in bs]
+
+    def batched_solve():
+        _, infos = B.solve(bs, params, out=xsol)
+        bad = [i for i in infos if i.status != 0 or i.true_res > bw["tol"]]
+        if bad:
+            raise RuntimeError(f"batched solve failed on {len(bad)} systems")
+        return infos
+
+    infos = batched_solve()
+    torch.cuda.synchronize()
+    counters(lib, reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = batched_solve()
+    e1.record(stream)
+    e1.synchronize()
+    t_b = e0.elapsed_time(e1) / 1e3
+    nl, nb = counters(lib, reset=True)
+
+    def sequential():
+        res = []
+        for op, b, nr in zip(ops, bs, nrhs):
+            for q in range(nr):
+                _, inf = op.solve(b[q], params)
+                res.append(inf)
+        return res
+
+    sequential()
+    torch.cuda.synchronize()
+    counters(lib, reset=True)
+    e0.record(stream)
+    seq = sequential()
+    e1.record(stream)
+    e1.synchronize()
+    t_s = e0.elapsed_time(e1) / 1e3
+    nl_s, nb_s = counters(lib, reset=True)
+    out["solve_batched"] = {"ms": 1e3 * t_b, "systems": len(infos), "launches": nl, "gbs": nb / t_b / 1e9,
+                            "max_true_res": max(i.true_res for i in infos),
+                            "inner_iters_max": max(i.iters for i in infos)}
+    out["solve_sequential"] = {"ms": 1e3 * t_s, "launches": nl_s, "gbs": nb_s / t_s / 1e9,
+                               "max_true_res": max(i.true_res for i in seq)}
+    out["batched_over_sequential_speedup"] = t_s / t_b
+    del B
+    return out
+
+
+def bench_force(lib, stream):
+    """dS/dU for S = phi^+ (D^+ D)^-1 phi on 24^3 x 48 (two solves and the
+    force kernels)."""
+    import torch
+
+    from paper_2112_00501_gb300 import api, synth
+
+    fw = FORCE_WORKLOAD
+    dims = fw["dims"]
+    U = synth.gauge_field(dims, fw["eps"], synth.gauge_seed(fw["config_index"]))
+    phi = torch.from_numpy(synth.gaussian_spinor(dims, synth.source_seed(fw["config_index"]))).cuda()
+    lat = api.Lattice(dims, fw["block"], -1)
+    op = api.CloverOperator(api.Gauge(lat, torch.from_numpy(U).cuda(), storage_prec=fw["prec"],
+                                      compress=fw["compress"]), fw["kappa"], fw["csw"])
+    params = api.solve_params(method=2, precond=1, smoother_prec=fw["prec"], tol=1e-10, max_iter=500)
+    op.force(phi, params)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 3
+    e0.record(stream)
+    for _ in range(n):
+        g, S, info = op.force(phi, params)
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / n
+    V = synth.volume(dims)
+    return {"workload": f"{'x'.join(map(str, dims))}, eps={fw['eps']}, kappa={fw['kappa']}, c_sw={fw['csw']}, "
+                        f"two-level solves (FP32 smoother) to 1e-10",
+            "ms": 1e3 * t, "links_per_s": 4 * V / t, "solve_iters": info.iters}
+
+
 def profile_kernel(which):
     """A few launches of one kernel on 24^3 x 48 at the workload's storage format
     (working set above the L2 size, about 2 GB on the device), for ncu."""
@@ -224,6 +364,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-force", action="store_true")
     ap.add_argument("--profile-kernel", choices=["sap", "dslash"], default=None,
                     help="run only a few launches of one kernel on 24^3x48 (for ncu captures)")
     args = ap.parse_args()
@@ -382,6 +524,11 @@ def main():
         del op64, g64
     counters(lib, reset=True)
 
+    # ---------------- batched workload and link force (reported beside the headline)
+    batch = None if args.no_batch else bench_batch(lib, stream)
+    force = None if args.no_force else bench_force(lib, stream)
+    counters(lib, reset=True)
+
     # ---------------- reduce over ranks
     t_max = t_dev
     tot_bytes = nbytes
@@ -442,6 +589,8 @@ def main():
         "e2e": {"value": nbytes_e2e / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": V * 192,
                 "d2h_bytes_per_step": V * 192, "ms_per_step": 1e3 * t_e2e / args.steps},
         "bytes_per_site_iteration": bytes_per_site_iter,
+        "batched": batch,
+        "force": force,
     }
     if not args.no_cpu_baseline:
         dt, it, Vs, thr = oracle_solve_sample(CPU_SAMPLE_DIMS)

@@ -359,6 +359,17 @@ __device__ __forceinline__ void staged_hop_dir(const SL &U, int l, int nf, int n
 }
 
 // shared-memory bytes of the staged kernel for a domain of vb sites
+// thread blocks of 256 threads per SM the staged kernel's shared memory allows
+// (2 only for FP16 storage with 12-real links); the register bound follows
+template <class GA, class CL>
+__host__ __device__ constexpr int staged_min_ctas()
+{
+    return 2 * (256 * (Staged<GA>::BYTES + StagedC<CL>::BYTES + StagedC<CL>::SCALE + 2 * 12 * 8) + 400 + 1024) <=
+                   228 * 1024
+               ? 2
+               : 1;
+}
+
 template <class GA, class CL>
 static size_t staged_smem(int vb)
 {
@@ -373,7 +384,7 @@ __device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, cons
                                                 int rr);
 
 template <class SP, class GA, class CL>
-__global__ void __launch_bounds__(256, 2) k_sap_staged(Geom g, SP b, SP x, GA U, CL C, float kappa, int colour,
+__global__ void __launch_bounds__(256, staged_min_ctas<GA, CL>()) k_sap_staged(Geom g, SP b, SP x, GA U, CL C, float kappa, int colour,
                                                        int nmr, int x_zero, int *status)
 {
     sap_staged_body(g, b, x, U, C, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
@@ -814,8 +825,10 @@ __global__ void __launch_bounds__(1 << LVB, 2) k_sap_h16_batch(SapBatch<Spinor16
     sap_h16_body<LVB>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
 }
 
+// one block per SM: selecting the lattice at run time costs registers that a
+// 128-register bound would turn into spills
 template <class SP, class GA, class CL>
-__global__ void __launch_bounds__(256, 2) k_sap_staged_batch(SapBatch<SP, GA, CL> B, int colour, int nmr, int x_zero)
+__global__ void __launch_bounds__(256, 1) k_sap_staged_batch(SapBatch<SP, GA, CL> B, int colour, int nmr, int x_zero)
 {
     int k, jb, rr;
     batch_item(B, k, jb, rr);
