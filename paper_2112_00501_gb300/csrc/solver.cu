@@ -555,7 +555,6 @@ static int fbicgstab(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
 // e = sum_j gamma_j z_j with R gamma = alpha, R unit upper triangular with
 // R_ij = c_ij, applied once per inner solve.
 
-constexpr int CH32 = 8;  // FP32 accumulation chunk
 
 template <int NV>
 __device__ __forceinline__ void finish_reduce(double *acc, double (*sh)[RT / 32], bool *last, double *partial,
@@ -584,8 +583,14 @@ __device__ __forceinline__ void finish_reduce(double *acc, double (*sh)[RT / 32]
     }
 }
 
+// FP32 vectors are read as float4 (two complex entries per load).  Each thread
+// takes U4 independent float4 entries per step (grid stride apart, so a warp's
+// loads stay contiguous) to keep enough loads in flight to cover HBM latency;
+// its FP32 partial sums go to FP64 after every step (U4 calls = 2 U4 entries).
+constexpr int U4 = 4;
+
 template <int NV, class F>
-__global__ void __launch_bounds__(RT) k_reduce32(long long n, F f, double *partial, unsigned *counter, double *out)
+__global__ void __launch_bounds__(RT) k_reduce32(long long n4, F f, double *partial, unsigned *counter, double *out)
 {
     __shared__ double sh[NV][RT / 32];
     __shared__ bool last;
@@ -596,27 +601,73 @@ __global__ void __launch_bounds__(RT) k_reduce32(long long n, F f, double *parti
         acc[k] = 0;
         facc[k] = 0.f;
     }
-    int c = 0;
-    for (long long e = (long long)blockIdx.x * RT + threadIdx.x; e < n; e += (long long)gridDim.x * RT) {
-        f(e, facc);
-        if (++c == CH32) {
-            c = 0;
+    const long long stride = (long long)gridDim.x * RT;
+    long long e = (long long)blockIdx.x * RT + threadIdx.x;
+    for (; e + (U4 - 1) * stride < n4; e += U4 * stride) {
 #pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                acc[k] += (double)facc[k];
-                facc[k] = 0.f;
-            }
+        for (int u = 0; u < U4; ++u) f(e + u * stride, facc);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            acc[k] += (double)facc[k];
+            facc[k] = 0.f;
         }
     }
+    for (; e < n4; e += stride) f(e, facc);
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] += (double)facc[k];
     finish_reduce<NV>(acc, sh, &last, partial, counter, out);
 }
 
+template <class F>
+__global__ void __launch_bounds__(RT) k_map32(long long n4, F f)
+{
+    const long long stride = (long long)gridDim.x * RT;
+    long long e = (long long)blockIdx.x * RT + threadIdx.x;
+    for (; e + (U4 - 1) * stride < n4; e += U4 * stride)
+#pragma unroll
+        for (int u = 0; u < U4; ++u) f(e + u * stride);
+    for (; e < n4; e += stride) f(e);
+}
+
+// blocks for the FP32 vector kernels: every block resident at once (a whole
+// number of waves over the SMs), within the partial-sum area
+template <class K>
+static int grid32(K kern, long long n4)
+{
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, RT, 0);
+        if (sms < 1) sms = 1;
+        if (per < 1) per = 1;
+        while (per > 1 && sms * per > RGRID_MAX) --per;
+        cached = sms * per > RGRID_MAX ? RGRID_MAX : sms * per;
+    }
+    long long need = (n4 + (long long)RT * U4 - 1) / ((long long)RT * U4);
+    if (need < 1) need = 1;
+    return need < cached ? (int)need : cached;
+}
+
+// n: complex entries (even); f takes a float4 index
 template <int NV, class F>
 static int reduce32(long long n, F f, SolverWork *W, double *out, cudaStream_t s, double bytes)
 {
-    k_reduce32<NV><<<red_grid(n), RT, 0, s>>>(n, f, W->partial, W->counter, out);
+    const long long n4 = n / 2;
+    auto kern = k_reduce32<NV, F>;
+    kern<<<grid32(kern, n4), RT, 0, s>>>(n4, f, W->partial, W->counter, out);
+    MGC_CUDA(cudaGetLastError());
+    count(1, bytes);
+    return MGC_OK;
+}
+
+template <class F>
+static int map32(long long n, F f, cudaStream_t s, double bytes)
+{
+    const long long n4 = n / 2;
+    auto kern = k_map32<F>;
+    kern<<<grid32(kern, n4), RT, 0, s>>>(n4, f);
     MGC_CUDA(cudaGetLastError());
     count(1, bytes);
     return MGC_OK;
@@ -628,9 +679,22 @@ __device__ __forceinline__ void facc_dot(float *acc, float2 a, float2 b)
     acc[1] = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc[1]));
 }
 __device__ __forceinline__ void facc_n2(float *acc, float2 a) { acc[0] = fmaf(a.x, a.x, fmaf(a.y, a.y, acc[0])); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+// v -= c u for the two complex entries of a float4
+__device__ __forceinline__ void csub4(float4 &v, float2 c, float4 u)
+{
+    v.x -= c.x * u.x - c.y * u.y;
+    v.y -= c.x * u.y + c.y * u.x;
+    v.z -= c.x * u.z - c.y * u.w;
+    v.w -= c.x * u.w + c.y * u.z;
+}
 
 struct PtrList32 {
     const float2 *p[MAXM];
+};
+struct PtrList4 {
+    const float4 *p[MAXM];
 };
 struct CoefList {
     float2 c[MAXM];
@@ -690,16 +754,20 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
         for (int i0 = 0; i0 <= j; i0 += 8) {
             const int cnt = (j + 1 - i0 < 8) ? j + 1 - i0 : 8;
             // <L_q, w_j> with L = (w'_0 .. w'_{j-1}, r)
-            PtrList32 L{};
-            for (int q = 0; q < cnt; ++q) L.p[q] = (i0 + q < j) ? W->w32[i0 + q] : r;
-            const float2 *wv = wj;
+            PtrList4 L{};
+            for (int q = 0; q < cnt; ++q) L.p[q] = (const float4 *)((i0 + q < j) ? W->w32[i0 + q] : r);
+            const float4 *wv = (const float4 *)wj;
             MGC_TRY(reduce32<16>(
                 n,
                 [=] __device__(long long e, float *acc) {
-                    const float2 v = wv[e];
+                    const float4 v = wv[e];
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
-                        if (q < cnt) facc_dot(acc + 2 * q, L.p[q][e], v);
+                        if (q < cnt) {
+                            const float4 a = L.p[q][e];
+                            facc_dot(acc + 2 * q, lo2(a), lo2(v));
+                            facc_dot(acc + 2 * q, hi2(a), hi2(v));
+                        }
                 },
                 W, sc + S_BETA, s, 8.0 * n * (cnt + 1)));
             double h[16];
@@ -709,24 +777,24 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
         const zd rho = std::conj(d[j]);  // <w_j, r>
         // w'_j = w_j - sum_i c_i w'_i, c_i = d_i / ||w'_i||^2; ||w'_j||^2
         CoefList C{};
-        PtrList32 Lw{};
+        PtrList4 Lw{};
         for (int i = 0; i < j; ++i) {
             const zd c = d[i] / n2[i];
             R[i][j] = c;
             C.c[i] = make_float2((float)c.real(), (float)c.imag());
-            Lw.p[i] = W->w32[i];
+            Lw.p[i] = (const float4 *)W->w32[i];
         }
+        float4 *wj4 = (float4 *)wj;
         MGC_TRY(reduce32<1>(
             n,
             [=] __device__(long long e, float *acc) {
-                float2 v = wj[e];
-                for (int i = 0; i < j; ++i) {
-                    const float2 c = C.c[i], u = Lw.p[i][e];
-                    v.x -= c.x * u.x - c.y * u.y;
-                    v.y -= c.x * u.y + c.y * u.x;
-                }
-                wj[e] = v;
-                facc_n2(acc, v);
+                float4 v = wj4[e];
+#pragma unroll
+                for (int i = 0; i < MAXM; ++i)
+                    if (i < j) csub4(v, C.c[i], Lw.p[i][e]);
+                wj4[e] = v;
+                facc_n2(acc, lo2(v));
+                facc_n2(acc, hi2(v));
             },
             W, sc + S_NW, s, 8.0 * n * (j + 2)));
         double nw;
@@ -735,15 +803,15 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
         n2[j] = nw;
         alpha[j] = rho / nw;
         const float2 a = make_float2((float)alpha[j].real(), (float)alpha[j].imag());
+        float4 *r4 = (float4 *)r;
         MGC_TRY(reduce32<1>(
             n,
             [=] __device__(long long e, float *acc) {
-                const float2 u = wj[e];
-                float2 v = r[e];
-                v.x -= a.x * u.x - a.y * u.y;
-                v.y -= a.x * u.y + a.y * u.x;
-                r[e] = v;
-                facc_n2(acc, v);
+                float4 v = r4[e];
+                csub4(v, a, wj4[e]);
+                r4[e] = v;
+                facc_n2(acc, lo2(v));
+                facc_n2(acc, hi2(v));
             },
             W, sc + S_RR, s, 8.0 * n * 3));
         MGC_TRY(read_scalars(W, S_RR, 1, &rr, s));
@@ -808,25 +876,24 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
         iters += k;
         // e = sum_j gamma_j z_j in FP32 (into w32[0], free after the inner solve;
         // its rounding is far below the inner tolerance), then x += ||r|| e
-        PtrList32 Lz{};
+        PtrList4 Lz{};
         CoefList G{};
         for (int j = 0; j < k; ++j) {
-            Lz.p[j] = W->z32[j];
+            Lz.p[j] = (const float4 *)W->z32[j];
             G.c[j] = make_float2((float)gamma[j].real(), (float)gamma[j].imag());
         }
         float2 *esum = W->w32[0];
-        MGC_TRY(map(
+        float4 *esum4 = (float4 *)esum;
+        MGC_TRY(map32(
             n,
             [=] __device__(long long e) {
-                float sx = 0.f, sy = 0.f;
-                for (int j = 0; j < k; ++j) {
-                    const float2 c = G.c[j], z = Lz.p[j][e];
-                    sx += c.x * z.x - c.y * z.y;
-                    sy += c.x * z.y + c.y * z.x;
-                }
-                esum[e] = make_float2(sx, sy);
+                float4 acc4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < MAXM; ++j)
+                    if (j < k) csub4(acc4, make_float2(-G.c[j].x, -G.c[j].y), Lz.p[j][e]);
+                esum4[e] = acc4;
             },
-            s, (k + 1) / 2));
+            s, 8.0 * n * (k + 1)));
         MGC_TRY(launch_axpy_from32(op->gauge->lat->g, x, esum, std::sqrt(rr), 0.0, s));
         MGC_TRY(apply_D64(op, x, t, s));
         MGC_TRY(residual(op, r, b, t, S_RR, s));
