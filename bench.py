@@ -70,7 +70,7 @@ class ClockSampler:
     def __init__(self, gpu_id: str | None):
         self.proc = None
         self.lines = []
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
         if gpu_id:
             cmd += ["-i", gpu_id]
         try:
@@ -119,6 +119,20 @@ def gpu_uuid(dev):
         return u if u.startswith("GPU-") else "GPU-" + u
     except Exception:
         return None
+
+
+def reduce_over_ranks(dist, t_dev, t_e2e, nbytes, nbytes_e2e, device):
+    """Replicas: the job's time is the slowest rank's, its work the sum over
+    ranks.  Returns (t_max, t_e2e_max, total bytes, total e2e bytes)."""
+    if not dist:
+        return t_dev, t_e2e, nbytes, nbytes_e2e
+    import torch
+
+    tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    bb = torch.tensor([nbytes, nbytes_e2e], dtype=torch.float64, device=device)
+    dist.all_reduce(bb, op=dist.ReduceOp.SUM)
+    return float(tt[0]), float(tt[1]), float(bb[0]), float(bb[1])
 
 
 def counters(lib, reset=False):
@@ -365,7 +379,7 @@ def profile_kernel(which):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -539,15 +553,7 @@ def main():
     counters(lib, reset=True)
 
     # ---------------- reduce over ranks
-    t_max = t_dev
-    tot_bytes = nbytes
-    if dist:
-        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        bb = torch.tensor([nbytes, nbytes_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(bb, op=dist.ReduceOp.SUM)
-        t_max, t_e2e = float(tt[0]), float(tt[1])
-        tot_bytes, nbytes_e2e = float(bb[0]), float(bb[1])
+    t_max, t_e2e, tot_bytes, nbytes_e2e = reduce_over_ranks(dist, t_dev, t_e2e, nbytes, nbytes_e2e, "cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
