@@ -36,6 +36,9 @@
  *     x_B += e, where D_B is D with every hop that leaves B dropped
  *     (Dirichlet).  MR starts at e = 0 and takes exactly k steps
  *     p = D_B r, alpha = <p, r> / <p, p>, e += alpha r, r -= alpha p.
+ *   - Sec. 2, QWS: the clover-preconditioned operator A = C^-1 D, its SAP
+ *     with a fixed number of Jacobi iterations per block, and the QWS solver
+ *     (Richardson around BiCGStab on A M_SAP, source multiplied by C^-1).
  *   - Sec. 3: the outer solver is flexible (the paper's is flexible BiCGStab);
  *     FGCR with restarts and flexible BiCGStab are provided, both right
  *     preconditioned with n_cy SAP sweeps from x = 0.
@@ -598,6 +601,206 @@ void or_sap(const int *L, const int *Bd, int tbc, double kappa, const cplx *U, c
             }
         }
     free(r);
+}
+
+/* ------------------------------------------------------------------ */
+/* the clover-preconditioned operator A = C^-1 D and its SAP (Sec. 2)   */
+/* ------------------------------------------------------------------ */
+
+/* out = C^-1 in site by site (Ci holds C^-1 per site) */
+static void clover_inv_apply(long V, const cplx *Ci, const cplx *in, cplx *out)
+{
+    for (long x = 0; x < V; ++x)
+        for (int i = 0; i < 12; ++i) {
+            cplx a = 0;
+            for (int j = 0; j < 12; ++j) a += Ci[x * 144 + i * 12 + j] * in[x * 12 + j];
+            out[x * 12 + i] = a;
+        }
+}
+
+/*
+ * A psi with A = C^-1 D (QWS's operator, Sec. 2): D applied first, then C^-1
+ * at every site.  C is the clover field D uses, Ci its inverse.
+ */
+void or_apply_A(const int *L, int tbc, double kappa, const cplx *U, const cplx *C, const cplx *Ci,
+                const cplx *in, cplx *out)
+{
+    long V = vol4(L);
+    cplx *t = malloc(sizeof(cplx) * V * 12);
+    or_dirac(L, tbc, kappa, U, C, in, t, 0);
+    clover_inv_apply(V, Ci, t, out);
+    free(t);
+}
+
+/*
+ * nj Jacobi iterations on the domain system A_B e = r_b from e = 0, with
+ * A_B = C_B^-1 D_B (Dirichlet D_B) split as 1 - (1 - A_B): each iteration is
+ * e <- e + (r_b - A_B e).  The first iteration gives e = r_b.
+ */
+static void jacobi_block_impl(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U,
+                              const cplx *C, const cplx *Ci, const cplx *r_b, cplx *e_b, int nj)
+{
+    long VB = block_volume(Bd);
+    long n = VB * 12;
+    cplx *t = malloc(sizeof(cplx) * n);
+    for (long i = 0; i < n; ++i) e_b[i] = 0;
+    for (int k = 0; k < nj; ++k) {
+        dirac_block_impl(L, Bd, bc, kappa, U, C, 0, e_b, t, 0);
+        for (long l = 0; l < VB; ++l) {
+            const cplx *ci = Ci + block_site(L, Bd, bc, l) * 144;
+            for (int i = 0; i < 12; ++i) {
+                cplx a = 0;
+                for (int j = 0; j < 12; ++j) a += ci[i * 12 + j] * t[l * 12 + j];
+                e_b[l * 12 + i] += r_b[l * 12 + i] - a;
+            }
+        }
+    }
+    free(t);
+}
+
+void or_jacobi_block(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U, const cplx *C,
+                     const cplx *Ci, const cplx *r_b, cplx *e_b, int nj)
+{
+    jacobi_block_impl(L, Bd, bc, kappa, U, C, Ci, r_b, e_b, nj);
+}
+
+/*
+ * n_cy multiplicative SAP sweeps on A x = b (QWS's M_SAP for A, Sec. 2):
+ * colour 0 then colour 1, every block B of the colour gets
+ * x_B += Jacobi_nj(A_B, (b - A x)|_B).
+ */
+void or_sap_A(const int *L, const int *Bd, int tbc, double kappa, const cplx *U, const cplx *C, const cplx *Ci,
+              const cplx *b, cplx *x, int ncy, int nj)
+{
+    long V = vol4(L);
+    long VB = block_volume(Bd);
+    int NB[4];
+    long nblk = 1;
+    for (int mu = 0; mu < 4; ++mu) { NB[mu] = L[mu] / Bd[mu]; nblk *= NB[mu]; }
+    cplx *r = malloc(sizeof(cplx) * V * 12);
+    for (int cy = 0; cy < ncy; ++cy)
+        for (int colour = 0; colour < 2; ++colour) {
+            or_apply_A(L, tbc, kappa, U, C, Ci, x, r);
+            for (long i = 0; i < V * 12; ++i) r[i] = b[i] - r[i];
+#pragma omp parallel for schedule(dynamic)
+            for (long blk = 0; blk < nblk; ++blk) {
+                int bc[4];
+                long t = blk;
+                for (int mu = 0; mu < 4; ++mu) { bc[mu] = (int)(t % NB[mu]); t /= NB[mu]; }
+                if (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) continue;
+                cplx *rb = malloc(sizeof(cplx) * VB * 12);
+                cplx *eb = malloc(sizeof(cplx) * VB * 12);
+                for (long l = 0; l < VB; ++l) {
+                    long s = block_site(L, Bd, bc, l);
+                    for (int i = 0; i < 12; ++i) rb[l * 12 + i] = r[s * 12 + i];
+                }
+                jacobi_block_impl(L, Bd, bc, kappa, U, C, Ci, rb, eb, nj);
+                for (long l = 0; l < VB; ++l) {
+                    long s = block_site(L, Bd, bc, l);
+                    for (int i = 0; i < 12; ++i) x[s * 12 + i] += eb[l * 12 + i];
+                }
+                free(rb);
+                free(eb);
+            }
+        }
+    free(r);
+}
+
+/*
+ * The QWS solver for D x = b (Sec. 2).  With A = C^-1 D the system is
+ * A x = C^-1 b.  Richardson iteration: r = C^-1 b - A x; solve
+ * (A M_SAP) y = r / ||r|| with BiCGStab to the relative residual inner_tol
+ * (M_SAP = n_cy sweeps of or_sap_A from zero with nj Jacobi iterations per
+ * block); x += ||r|| M_SAP y; stop when ||b - D x|| <= tol ||b|| (the true
+ * residual of D).  BiCGStab on K = A M_SAP from y = 0:
+ *   r = rhs, r0 = r, p = r, rho = <r0, r>; then v = K p,
+ *   alpha = rho / <r0, v>, s = r - alpha v, t = K s, omega = <t, s>/<t, t>,
+ *   y += alpha p + omega s, r = s - omega t, rho' = <r0, r>,
+ *   beta = (rho'/rho)(alpha/omega), p = r + beta (p - omega v).
+ * Returns 0 when converged; *iters counts BiCGStab iterations.
+ */
+typedef struct {
+    const int *L, *Bd;
+    int tbc;
+    double kappa;
+    const cplx *U, *C, *Ci;
+    int ncy, nj;
+} qws_t;
+
+static void qws_M(const qws_t *q, const cplx *v, cplx *z, long n)
+{
+    for (long i = 0; i < n; ++i) z[i] = 0;
+    or_sap_A(q->L, q->Bd, q->tbc, q->kappa, q->U, q->C, q->Ci, v, z, q->ncy, q->nj);
+}
+
+static void qws_K(const qws_t *q, const cplx *v, cplx *out, cplx *tmp, long n)
+{
+    qws_M(q, v, tmp, n);
+    or_apply_A(q->L, q->tbc, q->kappa, q->U, q->C, q->Ci, tmp, out);
+}
+
+int or_solve_qws(const int *L, const int *Bd, int tbc, double kappa, const cplx *U, const cplx *C, const cplx *Ci,
+                 const cplx *b, cplx *x, int ncy, int nj, double tol, double inner_tol, int max_iter, int *iters_out,
+                 double *res_out)
+{
+    qws_t q = {L, Bd, tbc, kappa, U, C, Ci, ncy, nj};
+    long V = vol4(L), n = V * 12;
+    cplx *r = malloc(sizeof(cplx) * n), *ra = malloc(sizeof(cplx) * n), *rhs = malloc(sizeof(cplx) * n);
+    cplx *y = malloc(sizeof(cplx) * n), *rr = malloc(sizeof(cplx) * n), *r0 = malloc(sizeof(cplx) * n);
+    cplx *p = malloc(sizeof(cplx) * n), *v = malloc(sizeof(cplx) * n), *s = malloc(sizeof(cplx) * n);
+    cplx *t = malloc(sizeof(cplx) * n), *tmp = malloc(sizeof(cplx) * n), *e = malloc(sizeof(cplx) * n);
+    double bnorm = sqrt(vnorm2(n, b));
+    int iters = 0, status = 1;
+    double rel = 0;
+    if (bnorm == 0) {
+        for (long i = 0; i < n; ++i) x[i] = 0;
+        status = 0;
+        goto done;
+    }
+    for (;;) {
+        /* true residual of D, then the residual of A */
+        or_dirac(L, tbc, kappa, U, C, x, tmp, 0);
+        for (long i = 0; i < n; ++i) r[i] = b[i] - tmp[i];
+        rel = sqrt(vnorm2(n, r)) / bnorm;
+        if (rel <= tol) { status = 0; break; }
+        if (iters >= max_iter) break;
+        clover_inv_apply(V, Ci, r, ra);
+        double rn = sqrt(vnorm2(n, ra));
+        for (long i = 0; i < n; ++i) rhs[i] = ra[i] / rn;
+        /* BiCGStab on (A M) y = rhs */
+        for (long i = 0; i < n; ++i) { y[i] = 0; rr[i] = rhs[i]; r0[i] = rhs[i]; p[i] = rhs[i]; }
+        cplx rho = vdot(n, r0, rr);
+        while (iters < max_iter) {
+            qws_K(&q, p, v, tmp, n);
+            cplx r0v = vdot(n, r0, v);
+            if (r0v == 0) break;
+            cplx alpha = rho / r0v;
+            for (long i = 0; i < n; ++i) s[i] = rr[i] - alpha * v[i];
+            qws_K(&q, s, t, tmp, n);
+            double tt = vnorm2(n, t);
+            cplx omega = (tt > 0) ? vdot(n, t, s) / tt : 0;
+            for (long i = 0; i < n; ++i) {
+                y[i] += alpha * p[i] + omega * s[i];
+                rr[i] = s[i] - omega * t[i];
+            }
+            ++iters;
+            if (sqrt(vnorm2(n, rr)) <= inner_tol) break;
+            cplx rho1 = vdot(n, r0, rr);
+            if (rho == 0 || omega == 0) break;
+            cplx beta = (rho1 / rho) * (alpha / omega);
+            for (long i = 0; i < n; ++i) p[i] = rr[i] + beta * (p[i] - omega * v[i]);
+            rho = rho1;
+        }
+        /* x += ||r|| M y */
+        qws_M(&q, y, e, n);
+        for (long i = 0; i < n; ++i) x[i] += rn * e[i];
+    }
+done:
+    *iters_out = iters;
+    *res_out = rel;
+    free(r); free(ra); free(rhs); free(y); free(rr); free(r0); free(p); free(v); free(s); free(t); free(tmp);
+    free(e);
+    return status;
 }
 
 /* ------------------------------------------------------------------ */

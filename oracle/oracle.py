@@ -54,6 +54,13 @@ def lib():
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.or_solve.restype = C.c_int
         L.or_force.argtypes = [_i4, C.c_int, C.c_double, C.c_double, _c16, _c16, _c16, _c16]
+        L.or_apply_A.argtypes = [_i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, _c16]
+        L.or_jacobi_block.argtypes = [_i4, _i4, _i4, C.c_double, _c16, _c16, _c16, _c16, _c16, C.c_int]
+        L.or_sap_A.argtypes = [_i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, _c16, C.c_int, C.c_int]
+        L.or_solve_qws.argtypes = [_i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, _c16, C.c_int,
+                                   C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                   C.POINTER(C.c_double)]
+        L.or_solve_qws.restype = C.c_int
         _lib = L
     return _lib
 
@@ -238,6 +245,49 @@ def solve(dims, bdims, tbc, kappa, U, Cl, b, method="fgcr", precond="sap", ncy=4
                         {"fgcr": 0, "fbicgstab": 1}[method], {"none": 0, "sap": 1}[precond],
                         int(ncy), int(nmr), int(m), float(tol), int(max_iter), C.byref(it),
                         C.byref(res))
+    return x, int(st), int(it.value), float(res.value)
+
+
+def apply_A(dims, tbc, kappa, U, Cl, Ci, psi):
+    """A psi with A = C^-1 D (the clover-preconditioned operator of Sec. 2)."""
+    V = _vol(dims)
+    psi = _sized(psi, V * 12, "psi")
+    out = np.zeros_like(psi)
+    lib().or_apply_A(_dims(dims), int(tbc), float(kappa), _sized(U, V * 36, "U"), _sized(Cl, V * 144, "Cl"),
+                     _sized(Ci, V * 144, "Ci"), psi, out)
+    return out
+
+
+def jacobi_block(dims, bdims, bc, kappa, U, Cl, Ci, r, nj):
+    """nj Jacobi iterations e <- e + (r - A_B e) from e = 0 on one domain."""
+    V = _vol(dims)
+    r = _sized(r, _vb(bdims) * 12, "r")
+    e = np.zeros_like(r)
+    lib().or_jacobi_block(_dims(dims), _dims(bdims), _dims(bc), float(kappa), _sized(U, V * 36, "U"),
+                          _sized(Cl, V * 144, "Cl"), _sized(Ci, V * 144, "Ci"), r, e, int(nj))
+    return e
+
+
+def sap_A(dims, bdims, tbc, kappa, U, Cl, Ci, b, x0=None, ncy=4, nj=4):
+    """n_cy multiplicative SAP sweeps on A x = b with nj Jacobi iterations per domain."""
+    V = _vol(dims)
+    b = _sized(b, V * 12, "b")
+    x = np.zeros_like(b) if x0 is None else _sized(np.array(x0, dtype=np.complex128, copy=True), V * 12, "x0")
+    lib().or_sap_A(_dims(dims), _dims(bdims), int(tbc), float(kappa), _sized(U, V * 36, "U"),
+                   _sized(Cl, V * 144, "Cl"), _sized(Ci, V * 144, "Ci"), b, x, int(ncy), int(nj))
+    return x
+
+
+def solve_qws(dims, bdims, tbc, kappa, U, Cl, Ci, b, ncy=4, nj=4, tol=1e-10, inner_tol=1e-6, max_iter=1000):
+    """The QWS solver of Sec. 2 for D x = b.  Returns (x, status, BiCGStab iterations, true residual)."""
+    V = _vol(dims)
+    b = _sized(b, V * 12, "b")
+    x = np.zeros_like(b)
+    it = C.c_int(0)
+    res = C.c_double(0)
+    st = lib().or_solve_qws(_dims(dims), _dims(bdims), int(tbc), float(kappa), _sized(U, V * 36, "U"),
+                            _sized(Cl, V * 144, "Cl"), _sized(Ci, V * 144, "Ci"), b, x, int(ncy), int(nj),
+                            float(tol), float(inner_tol), int(max_iter), C.byref(it), C.byref(res))
     return x, int(st), int(it.value), float(res.value)
 
 
