@@ -168,8 +168,8 @@ int mgc_apply_Ddag(mgc_clover_t op, const void *in, void *out, int nrhs, int pre
 
 /*
  * out = C in (inverse = 0) or C^-1 in (inverse = 1), site-local two 6x6
- * Hermitian blocks (Eq. (1); C^-1 is what QWS applies before M_SAP, Sec. 3).
- * prec 64 uses C or C^-1; lower precisions support inverse = 0 only.
+ * Hermitian blocks (Eq. (1); C^-1 is what QWS applies before M_SAP, Sec. 3),
+ * at any precision the operator keeps.
  */
 int mgc_apply_clover(mgc_clover_t op, const void *in, void *out, int nrhs, int prec, int inverse,
                      void *stream);
@@ -186,6 +186,24 @@ int mgc_sap_smooth(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, 
                    int prec, int x_is_zero, void *stream);
 
 /*
+ * QWS's clover-preconditioned operator (Sec. 2): out = A in with
+ * A = C^-1 D = 1 - kappa C^-1 H, for nrhs packed spinors at precision prec
+ * (64, or 32/16 when the gauge keeps that copy).  Asynchronous.
+ */
+int mgc_apply_A(mgc_clover_t op, const void *in, void *out, int nrhs, int prec, void *stream);
+
+/*
+ * QWS's M_SAP for A (Sec. 2): n_cy multiplicative sweeps (red domains, then
+ * black) on A x = b, each domain B getting x_B += e with e from n_jacobi
+ * Jacobi iterations e <- r_B + kappa C_B^-1 H_B e on the Dirichlet domain
+ * operator A_B from e = 0, r_B = (b - A x)|_B.  x (packed, prec) is updated in
+ * place; x_is_zero = 1 promises x == 0 on entry.  prec 64 computes in FP64;
+ * 32 and 16 compute in FP32.  Asynchronous.
+ */
+int mgc_sap_smooth_A(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, int n_jacobi, int prec,
+                     int x_is_zero, void *stream);
+
+/*
  * Solver parameters (Sec. 3: flexible outer solver with the SAP smoother as
  * preconditioner; Sec. 2: QWS's double-precision Richardson iteration around a
  * single-precision solver).  Methods:
@@ -193,7 +211,10 @@ int mgc_sap_smooth(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, 
  *   1  flexible BiCGStab (the paper's outer solver) with FP64 vectors;
  *   2  two-level: FP64 defect correction (residual b - D x, D and x in FP64)
  *      around an FP32 FGCR(restart) + SAP inner solve to inner_tol, whose
- *      inner products accumulate in FP64 across the lattice.
+ *      inner products accumulate in FP64 across the lattice;
+ *   3  QWS (Sec. 2): FP64 Richardson on b - D x around an FP32 BiCGStab on
+ *      A M_SAP (A = C^-1 D, source C^-1 r, M_SAP from mgc_sap_smooth_A with
+ *      n_mr Jacobi iterations per domain) to inner_tol; x += ||C^-1 r|| M_SAP y.
  */
 typedef struct {
     int method;        /* 0, 1 or 2 (above) */

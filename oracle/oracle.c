@@ -638,16 +638,16 @@ void or_apply_A(const int *L, int tbc, double kappa, const cplx *U, const cplx *
  * e <- e + (r_b - A_B e).  The first iteration gives e = r_b.
  */
 static void jacobi_block_impl(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U,
-                              const cplx *C, const cplx *Ci, const cplx *r_b, cplx *e_b, int nj)
+                              const cplx *C, const cplx *Ci, int compact, const cplx *r_b, cplx *e_b, int nj)
 {
     long VB = block_volume(Bd);
     long n = VB * 12;
     cplx *t = malloc(sizeof(cplx) * n);
     for (long i = 0; i < n; ++i) e_b[i] = 0;
     for (int k = 0; k < nj; ++k) {
-        dirac_block_impl(L, Bd, bc, kappa, U, C, 0, e_b, t, 0);
+        dirac_block_impl(L, Bd, bc, kappa, U, C, compact, e_b, t, 0);
         for (long l = 0; l < VB; ++l) {
-            const cplx *ci = Ci + block_site(L, Bd, bc, l) * 144;
+            const cplx *ci = Ci + (compact ? l : block_site(L, Bd, bc, l)) * 144;
             for (int i = 0; i < 12; ++i) {
                 cplx a = 0;
                 for (int j = 0; j < 12; ++j) a += ci[i * 12 + j] * t[l * 12 + j];
@@ -661,7 +661,24 @@ static void jacobi_block_impl(const int *L, const int *Bd, const int *bc, double
 void or_jacobi_block(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U, const cplx *C,
                      const cplx *Ci, const cplx *r_b, cplx *e_b, int nj)
 {
-    jacobi_block_impl(L, Bd, bc, kappa, U, C, Ci, r_b, e_b, nj);
+    jacobi_block_impl(L, Bd, bc, kappa, U, C, Ci, 0, r_b, e_b, nj);
+}
+
+/* the same Jacobi iterations on one block with the block's C and C^-1 built
+ * on the fly from U (for lattices whose full clover field is too large) */
+void or_jacobi_block_at(const int *L, const int *Bd, const int *bc, double kappa, double csw, const cplx *U,
+                        const cplx *r_b, cplx *e_b, int nj)
+{
+    long VB = block_volume(Bd);
+    cplx *Cb = malloc(sizeof(cplx) * VB * 144);
+    cplx *Cib = malloc(sizeof(cplx) * VB * 144);
+    for (long l = 0; l < VB; ++l) {
+        or_clover_site(L, kappa, csw, U, block_site(L, Bd, bc, l), Cb + l * 144);
+        or_invert(12, Cb + l * 144, Cib + l * 144);
+    }
+    jacobi_block_impl(L, Bd, bc, kappa, U, Cb, Cib, 1, r_b, e_b, nj);
+    free(Cb);
+    free(Cib);
 }
 
 /*
@@ -694,7 +711,7 @@ void or_sap_A(const int *L, const int *Bd, int tbc, double kappa, const cplx *U,
                     long s = block_site(L, Bd, bc, l);
                     for (int i = 0; i < 12; ++i) rb[l * 12 + i] = r[s * 12 + i];
                 }
-                jacobi_block_impl(L, Bd, bc, kappa, U, C, Ci, rb, eb, nj);
+                jacobi_block_impl(L, Bd, bc, kappa, U, C, Ci, 0, rb, eb, nj);
                 for (long l = 0; l < VB; ++l) {
                     long s = block_site(L, Bd, bc, l);
                     for (int i = 0; i < 12; ++i) x[s * 12 + i] += eb[l * 12 + i];

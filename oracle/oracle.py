@@ -56,6 +56,7 @@ def lib():
         L.or_force.argtypes = [_i4, C.c_int, C.c_double, C.c_double, _c16, _c16, _c16, _c16]
         L.or_apply_A.argtypes = [_i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, _c16]
         L.or_jacobi_block.argtypes = [_i4, _i4, _i4, C.c_double, _c16, _c16, _c16, _c16, _c16, C.c_int]
+        L.or_jacobi_block_at.argtypes = [_i4, _i4, _i4, C.c_double, C.c_double, _c16, _c16, _c16, C.c_int]
         L.or_sap_A.argtypes = [_i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, _c16, C.c_int, C.c_int]
         L.or_solve_qws.argtypes = [_i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, _c16, C.c_int,
                                    C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -265,6 +266,15 @@ def jacobi_block(dims, bdims, bc, kappa, U, Cl, Ci, r, nj):
     e = np.zeros_like(r)
     lib().or_jacobi_block(_dims(dims), _dims(bdims), _dims(bc), float(kappa), _sized(U, V * 36, "U"),
                           _sized(Cl, V * 144, "Cl"), _sized(Ci, V * 144, "Ci"), r, e, int(nj))
+    return e
+
+
+def jacobi_block_at(dims, bdims, bc, kappa, csw, U, r, nj):
+    """Jacobi on one domain with its C and C^-1 built on the fly (no full clover field)."""
+    r = _sized(r, _vb(bdims) * 12, "r")
+    e = np.zeros_like(r)
+    lib().or_jacobi_block_at(_dims(dims), _dims(bdims), _dims(bc), float(kappa), float(csw),
+                             _sized(U, _vol(dims) * 36, "U"), r, e, int(nj))
     return e
 
 

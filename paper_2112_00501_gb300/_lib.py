@@ -74,6 +74,8 @@ SIGNATURES = {
     "mgc_apply_Ddag": (_I, [_P, _P, _P, _I, _I, _P]),
     "mgc_apply_clover": (_I, [_P, _P, _P, _I, _I, _I, _P]),
     "mgc_sap_smooth": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P]),
+    "mgc_apply_A": (_I, [_P, _P, _P, _I, _I, _P]),
+    "mgc_sap_smooth_A": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P]),
     "mgc_solve_params_default": (None, [C.POINTER(SolveParams)]),
     "mgc_solve": (_I, [_P, _P, _P, _I, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P]),
     "mgc_force": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(SolveInfo), C.POINTER(_D), _P]),

@@ -172,6 +172,36 @@ class CloverOperator:
                                       _stream(stream)), "mgc_sap_smooth")
         return x
 
+    def apply_A(self, x: torch.Tensor, prec: int, nrhs: int = 1, out=None, stream=None) -> torch.Tensor:
+        """A x with A = C^-1 D (QWS's operator), packed fields."""
+        if out is None:
+            out = self.lattice.empty_packed(prec, nrhs)
+        check(self.lib.mgc_apply_A(self.handle, _ptr(x), _ptr(out), nrhs, prec, _stream(stream)), "mgc_apply_A")
+        return out
+
+    def sap_smooth_A(self, b: torch.Tensor, x: torch.Tensor, prec: int, nrhs: int = 1, n_cy: int = 4,
+                     n_jacobi: int = 4, x_is_zero: bool = False, stream=None) -> torch.Tensor:
+        """QWS's M_SAP for A: n_cy sweeps with n_jacobi Jacobi iterations per domain, packed fields."""
+        check(self.lib.mgc_sap_smooth_A(self.handle, _ptr(b), _ptr(x), nrhs, n_cy, n_jacobi, prec,
+                                        int(bool(x_is_zero)), _stream(stream)), "mgc_sap_smooth_A")
+        return x
+
+    def A(self, psi, prec: int = 64) -> torch.Tensor:
+        """A psi for canonical complex128 field(s), computed at prec."""
+        psi = _canon(psi, "cuda")
+        nrhs = 1 if psi.dim() == 3 else psi.shape[0]
+        x = self.lattice.pack(psi, prec)
+        return self.lattice.unpack(self.apply_A(x, prec, nrhs), prec, nrhs)
+
+    def sap_A(self, b, prec: int = 64, n_cy: int = 4, n_jacobi: int = 4, x0=None) -> torch.Tensor:
+        """n_cy SAP sweeps on A x = b from x0 (default 0), canonical in and out."""
+        b = _canon(b, "cuda")
+        nrhs = 1 if b.dim() == 3 else b.shape[0]
+        bp = self.lattice.pack(b, prec)
+        xp = self.lattice.zeros_packed(prec, nrhs) if x0 is None else self.lattice.pack(_canon(x0, "cuda"), prec)
+        self.sap_smooth_A(bp, xp, prec, nrhs, n_cy, n_jacobi, x_is_zero=x0 is None)
+        return self.lattice.unpack(xp, prec, nrhs)
+
     def export_clover(self, inverse=False, stream=None) -> torch.Tensor:
         out = torch.empty((self.lattice.volume, 12, 12), dtype=torch.complex128, device="cuda")
         check(self.lib.mgc_clover_export(self.handle, int(bool(inverse)), _ptr(out), _stream(stream)),

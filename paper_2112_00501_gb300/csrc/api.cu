@@ -269,6 +269,8 @@ int mgc_clover_create(mgc_gauge_t g, double kappa, double csw, void *stream, mgc
             cudaFree(op->Ci64);
             cudaFree(op->C32);
             cudaFree(op->C16);
+            cudaFree(op->Ci32);
+            cudaFree(op->Ci16);
             cudaFree(op->d_status);
             delete op;
         }
@@ -287,15 +289,24 @@ int mgc_clover_create(mgc_gauge_t g, double kappa, double csw, void *stream, mgc
     CCUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
     int st = launch_clover_build(geo, g->U64, kappa, csw, op->C64, op->Ci64, d_bad, s);
     if (st) return bail(st);
+    // C and C^-1 (the latter for the clover-preconditioned operator A = C^-1 D)
+    // at every precision the gauge field keeps
     if (g->prec <= 32) {
         CCUDA(cudaMalloc(&op->C32, clover_bytes(geo, 32)));
         st = launch_clover_lowprec(geo, op->C64, 32, op->C32, s);
+        if (st) return bail(st);
+        CCUDA(cudaMalloc(&op->Ci32, clover_bytes(geo, 32)));
+        st = launch_clover_lowprec(geo, op->Ci64, 32, op->Ci32, s);
         if (st) return bail(st);
     }
     if (g->prec == 16) {
         CCUDA(cudaMalloc(&op->C16, clover_bytes(geo, 16)));
         op->C16_sc = (float *)((uint4 *)op->C16 + (size_t)geo.V * 9);
         st = launch_clover_lowprec(geo, op->C64, 16, op->C16, s);
+        if (st) return bail(st);
+        CCUDA(cudaMalloc(&op->Ci16, clover_bytes(geo, 16)));
+        op->Ci16_sc = (float *)((uint4 *)op->Ci16 + (size_t)geo.V * 9);
+        st = launch_clover_lowprec(geo, op->Ci64, 16, op->Ci16, s);
         if (st) return bail(st);
     }
     int bad = 0;
@@ -315,6 +326,8 @@ int mgc_clover_destroy(mgc_clover_t op)
     cudaFree(op->Ci64);
     cudaFree(op->C32);
     cudaFree(op->C16);
+    cudaFree(op->Ci32);
+    cudaFree(op->Ci16);
     cudaFree(op->d_status);
     delete op;
     return MGC_OK;
@@ -373,6 +386,20 @@ int mgc_sap_smooth(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, 
     MGC_TRY(check_apply(op, b, x, nrhs, prec));
     if (n_cy < 0 || n_mr < 0) return fail(MGC_ERR_INVALID_ARG, "n_cy and n_mr must be >= 0");
     return launch_sap(op, prec, b, x, nrhs, n_cy, n_mr, x_is_zero, (cudaStream_t)stream);
+}
+
+int mgc_apply_A(mgc_clover_t op, const void *in, void *out, int nrhs, int prec, void *stream)
+{
+    MGC_TRY(check_apply(op, in, out, nrhs, prec));
+    return launch_apply_A(op, prec, in, out, nrhs, (cudaStream_t)stream);
+}
+
+int mgc_sap_smooth_A(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, int n_jacobi, int prec,
+                     int x_is_zero, void *stream)
+{
+    MGC_TRY(check_apply(op, b, x, nrhs, prec));
+    if (n_cy < 0 || n_jacobi < 0) return fail(MGC_ERR_INVALID_ARG, "n_cy and n_jacobi must be >= 0");
+    return launch_sap_A(op, prec, b, x, nrhs, n_cy, n_jacobi, x_is_zero, (cudaStream_t)stream);
 }
 
 void mgc_solve_params_default(mgc_solve_params *p)

@@ -267,6 +267,80 @@ int launch_dirac(const mgc_clover_s *op, int prec, bool dag, const void *in, voi
     return MGC_OK;
 }
 
+// ------------------------------------------------------------------ A = C^-1 D
+// QWS's clover-preconditioned operator (Sec. 2): A psi = psi - kappa C^-1 H psi,
+// one thread per site, the same hopping sum as k_dirac followed by C^-1.
+template <int LVB, class SP, class GA, class CL>
+__global__ void __launch_bounds__(256, (LVB > 0 && sizeof(typename SP::Real) == 4) ? 3 : 1)
+    k_apply_A(Geom g, SP in, SP out, GA U, CL Ci, typename SP::Real kappa)
+{
+    using T = typename SP::Real;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int r = blockIdx.y;
+    SP src = shift_rhs(in, r, g.V), dst = shift_rhs(out, r, g.V);
+    GA Ug = U;
+    CL Cg = Ci;
+    Geom gg = g;
+    if (LVB > 0) {
+        gg.lvb = LVB;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) gg.lb[mu] = LVB / 4;
+        src.lvb = dst.lvb = Ug.lvb = Cg.lvb = LVB;
+    }
+    int c[4];
+    site_coords(gg, i, c);
+    Cx<T> acc[12], t[12], psi[12];
+    hop_site<false>(gg, c, i, src, Ug, acc);
+    clover_site(Cg, i, acc, t);
+    src.load(i, psi);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) psi[k] = Cx<T>{fma(-kappa, t[k].r, psi[k].r), fma(-kappa, t[k].i, psi[k].i)};
+    dst.store(i, psi);
+}
+
+template <class SP, class GA, class CL>
+static void apply_A_dispatch(const Geom &g, SP in, SP out, GA U, CL Ci, double kappa, int nrhs, cudaStream_t s)
+{
+    using T = typename SP::Real;
+    const bool cube = g.lb[0] == g.lb[1] && g.lb[1] == g.lb[2] && g.lb[2] == g.lb[3];
+    dim3 grid(grid_for(g.V, 256), nrhs);
+    if (cube && g.lvb == 8) k_apply_A<8><<<grid, 256, 0, s>>>(g, in, out, U, Ci, (T)kappa);
+    else if (cube && g.lvb == 4) k_apply_A<4><<<grid, 256, 0, s>>>(g, in, out, U, Ci, (T)kappa);
+    else k_apply_A<0><<<grid, 256, 0, s>>>(g, in, out, U, Ci, (T)kappa);
+}
+
+int launch_apply_A(const mgc_clover_s *op, int prec, const void *in, void *out, int nrhs, cudaStream_t s)
+{
+    const mgc_gauge_s *ga = op->gauge;
+    const Geom &g = ga->lat->g;
+    if (!has_prec(ga, prec)) return fail(MGC_ERR_INVALID_ARG, "no copy of the operator at this precision");
+    if (prec == 64) {
+        apply_A_dispatch(g, sp64(g, in), sp64(g, out), Gauge64{ga->U64, g.lvb}, Clover64{op->Ci64, g.lvb}, op->kappa,
+                         nrhs, s);
+    } else if (prec == 32) {
+        Clover32 Ci{(float4 *)op->Ci32, g.lvb};
+        if (ga->compress == 12)
+            apply_A_dispatch(g, sp32(g, in), sp32(g, out), Gauge32x12{(float4 *)ga->U32, g.lvb}, Ci, op->kappa, nrhs,
+                             s);
+        else
+            apply_A_dispatch(g, sp32(g, in), sp32(g, out), Gauge32x18{(float2 *)ga->U32, g.lvb}, Ci, op->kappa, nrhs,
+                             s);
+    } else {
+        Clover16 Ci{(uint4 *)op->Ci16, op->Ci16_sc, g.lvb};
+        if (ga->compress == 12)
+            apply_A_dispatch(g, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x12{(uint2 *)ga->U16, g.lvb}, Ci,
+                             op->kappa, nrhs, s);
+        else
+            apply_A_dispatch(g, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x18{(uint32_t *)ga->U16, g.lvb}, Ci,
+                             op->kappa, nrhs, s);
+    }
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * (2.0 * nrhs * spinor_site_bytes(prec) +
+                            links_site_bytes(prec, prec == 64 ? 18 : ga->compress) + clover_site_bytes(prec)));
+    return MGC_OK;
+}
+
 // ------------------------------------------------------------------ clover apply
 template <class SP, class CL>
 __global__ void k_clover_apply(Geom g, SP in, SP out, CL C)
@@ -291,14 +365,14 @@ int launch_clover_apply(const mgc_clover_s *op, int prec, bool inverse, const vo
     if (prec == 64) {
         k_clover_apply<<<grid, 256, 0, s>>>(g, sp64(g, in), sp64(g, out),
                                             Clover64{inverse ? op->Ci64 : op->C64, g.lvb});
-    } else if (inverse) {
-        return fail(MGC_ERR_INVALID_ARG, "C^-1 is kept in FP64 only");
     } else if (!has_prec(op->gauge, prec)) {
         return fail(MGC_ERR_INVALID_ARG, "no copy of the clover term at this precision");
     } else if (prec == 32) {
-        k_clover_apply<<<grid, 256, 0, s>>>(g, sp32(g, in), sp32(g, out), Clover32{(float4 *)op->C32, g.lvb});
+        k_clover_apply<<<grid, 256, 0, s>>>(g, sp32(g, in), sp32(g, out),
+                                            Clover32{(float4 *)(inverse ? op->Ci32 : op->C32), g.lvb});
     } else {
-        k_clover_apply<<<grid, 256, 0, s>>>(g, sp16(g, in, nrhs), sp16(g, out, nrhs), cl16(g, op));
+        const Clover16 C = inverse ? Clover16{(uint4 *)op->Ci16, op->Ci16_sc, g.lvb} : cl16(g, op);
+        k_clover_apply<<<grid, 256, 0, s>>>(g, sp16(g, in, nrhs), sp16(g, out, nrhs), C);
     }
     MGC_CUDA(cudaGetLastError());
     count(1, (double)g.V * (2.0 * nrhs * spinor_site_bytes(prec) + clover_site_bytes(prec)));

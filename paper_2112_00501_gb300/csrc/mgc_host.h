@@ -39,6 +39,9 @@ struct mgc_clover_s {
     void *C32;      // packed FP32 C (NULL when prec == 64)
     void *C16;      // packed FP16 C followed by its per-site scales (prec == 16)
     float *C16_sc;
+    void *Ci32;     // C^-1 at FP32 and FP16 (same layouts), for A = C^-1 D
+    void *Ci16;
+    float *Ci16_sc;
     int *d_status;  // device status word: bits set by kernels whose bounded waits ran out
     mgc::SolverWork *work;
 };
@@ -99,6 +102,8 @@ int launch_dirac(const mgc_clover_s *op, int prec, bool dag, const void *in, voi
 int launch_clover_apply(const mgc_clover_s *op, int prec, bool inverse, const void *in, void *out, int nrhs,
                         cudaStream_t s);
 int launch_gamma5(const Geom &g, int nrhs, const double2 *in, double2 *out, cudaStream_t s);
+// out = A in with A = C^-1 D (QWS's clover-preconditioned operator)
+int launch_apply_A(const mgc_clover_s *op, int prec, const void *in, void *out, int nrhs, cudaStream_t s);
 // out (packed FP32) = s * in (packed FP64); x (packed FP64) += (cr + i ci) * e (packed FP32)
 int launch_scale_to32(const Geom &g, const double2 *in, void *out, double s, cudaStream_t st);
 int launch_axpy_from32(const Geom &g, double2 *x, const void *e, double cr, double ci, cudaStream_t st);
@@ -114,6 +119,9 @@ int launch_unitarity(const Geom &g, const double *canon_dev, double *d_maxerr, c
 int launch_sap(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_mr,
                int x_is_zero, cudaStream_t s);
 int selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, cudaStream_t s);
+// the smoother for A = C^-1 D: n_jacobi Jacobi iterations per domain
+int launch_sap_A(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_jacobi,
+                 int x_is_zero, cudaStream_t s);
 
 // solver.cu
 int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solve_params *p, mgc_solve_info *info,

@@ -11,6 +11,13 @@
 //   3. x_B += e.
 // Domains of one colour never touch each other, so the launches of a sweep
 // are red then black and every block of a launch is independent.
+//
+// With JAC = true the same kernels run QWS's smoother for the clover-
+// preconditioned operator A = C^-1 D = 1 - kappa C^-1 H (Sec. 2): the staged
+// clover term is C^-1, the domain residual is r_B = (b - x + kappa C^-1 H x)|_B,
+// and the domain solve is a fixed number n_j of Jacobi iterations
+// e <- r_B + kappa C^-1 H_B e from e = 0 (the first gives e = r_B), with e
+// (instead of r) in shared memory and no block reductions.
 #include "hop.cuh"
 #include "mgc_host.h"
 #include "tma.cuh"
@@ -74,7 +81,7 @@ __device__ __forceinline__ void block_hop_dir(const GA &U, int blkbase, int i, i
     }
 }
 
-template <class SP, class GA, class CL>
+template <bool JAC, class SP, class GA, class CL>
 __global__ void __launch_bounds__(256) k_sap_colour(Geom g, SP b, SP x, GA U, CL C, typename SP::Real kappa,
                                                     int colour, int nmr, int x_zero)
 {
@@ -107,14 +114,24 @@ __global__ void __launch_bounds__(256) k_sap_colour(Geom g, SP b, SP x, GA U, CL
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) c[mu] = (bc[mu] << g.lb[mu]) + lc[mu];
 
-    // 1. block residual
+    // 1. block residual (of D, or of A = C^-1 D with C holding C^-1)
     Cx<T> rv[12];
     bb.load(i, rv);
     if (!x_zero) {
-        Cx<T> dx[12];
-        dirac_site<false>(g, c, i, xx, U, C, kappa, dx);
+        if (JAC) {
+            Cx<T> acc[12], t[12], xo[12];
+            hop_site<false>(g, c, i, xx, U, acc);
+            clover_site(C, i, acc, t);
+            xx.load(i, xo);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) rv[k] = rv[k] - dx[k];
+            for (int k = 0; k < 12; ++k)
+                rv[k] = Cx<T>{fma(kappa, t[k].r, rv[k].r - xo[k].r), fma(kappa, t[k].i, rv[k].i - xo[k].i)};
+        } else {
+            Cx<T> dx[12];
+            dirac_site<false>(g, c, i, xx, U, C, kappa, dx);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rv[k] = rv[k] - dx[k];
+        }
     }
     // in-domain neighbours (local index, or -1 when the hop leaves the domain)
     int nf[4], nb[4];
@@ -132,6 +149,31 @@ __global__ void __launch_bounds__(256) k_sap_colour(Geom g, SP b, SP x, GA U, CL
 #pragma unroll
     for (int k = 0; k < 12; ++k) e[k] = Cx<T>{0, 0};
     __syncthreads();
+
+    // 2'. Jacobi on A_B: e_1 = r_B, then e <- r_B + kappa C^-1 H_B e
+    if (JAC) {
+        if (nmr >= 1)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) e[k] = rv[k];
+        for (int it = 1; it < nmr; ++it) {
+            Cx<T> acc[12], t[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k] = Cx<T>{0, 0};
+            block_hop_dir<0>(U, blkbase, i, nf[0], nb[0], rs, vb, acc);
+            block_hop_dir<1>(U, blkbase, i, nf[1], nb[1], rs, vb, acc);
+            block_hop_dir<2>(U, blkbase, i, nf[2], nb[2], rs, vb, acc);
+            block_hop_dir<3>(U, blkbase, i, nf[3], nb[3], rs, vb, acc);
+            clover_site(C, i, acc, t);
+            __syncthreads();  // every thread has read e before it is replaced
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                e[k] = Cx<T>{fma(kappa, t[k].r, rv[k].r), fma(kappa, t[k].i, rv[k].i)};
+                rs[k * vb + l] = e[k];
+            }
+            __syncthreads();
+        }
+        nmr = 0;
+    }
 
     // 2. minimal residual on D_B
     for (int it = 0; it < nmr; ++it) {
@@ -378,19 +420,19 @@ static size_t staged_smem(int vb)
 }
 
 // one domain solve of the staged kernel: domain jb of `colour`, right-hand side rr
-template <class SP, class GA, class CL>
+template <bool JAC, class SP, class GA, class CL>
 __device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, const SP &x, const GA &U, const CL &C,
                                                 float kappa, int colour, int nmr, int x_zero, int *status, int jb,
                                                 int rr);
 
-template <class SP, class GA, class CL>
-__global__ void __launch_bounds__(256, staged_min_ctas<GA, CL>()) k_sap_staged(Geom g, SP b, SP x, GA U, CL C, float kappa, int colour,
-                                                       int nmr, int x_zero, int *status)
+template <bool JAC, class SP, class GA, class CL>
+__global__ void __launch_bounds__(256, staged_min_ctas<GA, CL>())
+    k_sap_staged(Geom g, SP b, SP x, GA U, CL C, float kappa, int colour, int nmr, int x_zero, int *status)
 {
-    sap_staged_body(g, b, x, U, C, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
+    sap_staged_body<JAC>(g, b, x, U, C, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
 }
 
-template <class SP, class GA, class CL>
+template <bool JAC, class SP, class GA, class CL>
 __device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, const SP &x, const GA &U, const CL &C,
                                                 float kappa, int colour, int nmr, int x_zero, int *status, int jb,
                                                 int rr)
@@ -465,10 +507,18 @@ __device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, cons
     if (!x_zero) {
         Cx<float> cx[12];
         xx.load(i, xs);
-        Cs.mul(l, xs, cx);
+        if (JAC) {
+            Cs.mul(l, acc, cx);  // C^-1 H x
 #pragma unroll
-        for (int k = 0; k < 12; ++k)
-            rv[k] = Cx<float>{rv[k].r - fmaf(-kappa, acc[k].r, cx[k].r), rv[k].i - fmaf(-kappa, acc[k].i, cx[k].i)};
+            for (int k = 0; k < 12; ++k)
+                rv[k] = Cx<float>{fmaf(kappa, cx[k].r, rv[k].r - xs[k].r), fmaf(kappa, cx[k].i, rv[k].i - xs[k].i)};
+        } else {
+            Cs.mul(l, xs, cx);
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                rv[k] = Cx<float>{rv[k].r - fmaf(-kappa, acc[k].r, cx[k].r),
+                                  rv[k].i - fmaf(-kappa, acc[k].i, cx[k].i)};
+        }
     }
     int nf[4], nb[4];
 #pragma unroll
@@ -485,6 +535,29 @@ __device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, cons
         es[k * vb + l] = Cx<float>{0.f, 0.f};
     }
     __syncthreads();
+
+    // 2'. Jacobi on A_B with e in shared memory (rs): e_1 = r_B, then
+    // e <- r_B + kappa C^-1 H_B e
+    if (JAC) {
+        for (int it = 1; it < nmr; ++it) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k] = Cx<float>{0.f, 0.f};
+            staged_hop_dir<0>(Us, l, nf[0], nb[0], rs, vb, acc);
+            staged_hop_dir<1>(Us, l, nf[1], nb[1], rs, vb, acc);
+            staged_hop_dir<2>(Us, l, nf[2], nb[2], rs, vb, acc);
+            staged_hop_dir<3>(Us, l, nf[3], nb[3], rs, vb, acc);
+            Cx<float> t[12];
+            Cs.mul(l, acc, t);
+            __syncthreads();  // every thread has read e before it is replaced
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                rs[k * vb + l] = Cx<float>{fmaf(kappa, t[k].r, rv[k].r), fmaf(kappa, t[k].i, rv[k].i)};
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) es[k * vb + l] = nmr >= 1 ? rs[k * vb + l] : Cx<float>{0.f, 0.f};
+        nmr = 0;
+    }
 
     // 2. minimal residual on D_B with links, clover and r in shared memory
     for (int it = 0; it < nmr; ++it) {
@@ -575,19 +648,19 @@ __device__ __forceinline__ void h16_hop(const float4 *rs, int n, const uint32_t 
 }
 
 // one domain solve of the FP16 kernel: domain jb of `colour`, right-hand side rr
-template <int LVB, class GA>
+template <bool JAC, int LVB, class GA>
 __device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, const Spinor16 &x, const GA &U,
                                              const Clover16 &C, float kappa, int colour, int nmr, int x_zero,
                                              int *status, int jb, int rr);
 
-template <int LVB, class GA>
+template <bool JAC, int LVB, class GA>
 __global__ void __launch_bounds__(1 << LVB, 2) k_sap_h16(Geom g, Spinor16 b, Spinor16 x, GA U, Clover16 C, float kappa,
                                                          int colour, int nmr, int x_zero, int *status)
 {
-    sap_h16_body<LVB>(g, b, x, U, C, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
+    sap_h16_body<JAC, LVB>(g, b, x, U, C, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
 }
 
-template <int LVB, class GA>
+template <bool JAC, int LVB, class GA>
 __device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, const Spinor16 &x, const GA &U,
                                              const Clover16 &C, float kappa, int colour, int nmr, int x_zero,
                                              int *status, int jb, int rr)
@@ -678,10 +751,18 @@ __device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, c
     if (!x_zero) {
         Cx<float> xs[12], cx[12];
         xx.load(i, xs);
-        Cs.mul(l, xs, cx);
+        if (JAC) {
+            Cs.mul(l, acc, cx);  // C^-1 H x
 #pragma unroll
-        for (int k = 0; k < 12; ++k)
-            rv[k] = Cx<float>{rv[k].r - fmaf(-kappa, acc[k].r, cx[k].r), rv[k].i - fmaf(-kappa, acc[k].i, cx[k].i)};
+            for (int k = 0; k < 12; ++k)
+                rv[k] = Cx<float>{fmaf(kappa, cx[k].r, rv[k].r - xs[k].r), fmaf(kappa, cx[k].i, rv[k].i - xs[k].i)};
+        } else {
+            Cs.mul(l, xs, cx);
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                rv[k] = Cx<float>{rv[k].r - fmaf(-kappa, acc[k].r, cx[k].r),
+                                  rv[k].i - fmaf(-kappa, acc[k].i, cx[k].i)};
+        }
     }
     int nf[4], nb[4];
 #pragma unroll
@@ -698,6 +779,36 @@ __device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, c
 #pragma unroll
     for (int k = 0; k < 12; ++k) e[k] = Cx<float>{0.f, 0.f};
     __syncthreads();
+
+    // 2'. Jacobi on A_B with e in shared memory (rs): e_1 = r_B, then
+    // e <- r_B + kappa C^-1 H_B e
+    if (JAC) {
+        if (nmr >= 1)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) e[k] = rv[k];
+        for (int it = 1; it < nmr; ++it) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k] = Cx<float>{0.f, 0.f};
+            if (nf[0] >= 0) h16_hop<0, -1, VB>(rs, nf[0], sL, l, acc);
+            if (nb[0] >= 0) h16_hop<0, +1, VB>(rs, nb[0], sL, nb[0], acc);
+            if (nf[1] >= 0) h16_hop<1, -1, VB>(rs, nf[1], sL, l, acc);
+            if (nb[1] >= 0) h16_hop<1, +1, VB>(rs, nb[1], sL, nb[1], acc);
+            if (nf[2] >= 0) h16_hop<2, -1, VB>(rs, nf[2], sL, l, acc);
+            if (nb[2] >= 0) h16_hop<2, +1, VB>(rs, nb[2], sL, nb[2], acc);
+            if (nf[3] >= 0) h16_hop<3, -1, VB>(rs, nf[3], sL, l, acc);
+            if (nb[3] >= 0) h16_hop<3, +1, VB>(rs, nb[3], sL, nb[3], acc);
+            Cx<float> t[12];
+            Cs.mul(l, acc, t);
+            __syncthreads();  // every thread has read e before it is replaced
+#pragma unroll
+            for (int k = 0; k < 12; ++k) e[k] = Cx<float>{fmaf(kappa, t[k].r, rv[k].r), fmaf(kappa, t[k].i, rv[k].i)};
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                rs[k * VB + l] = make_float4(e[2 * k].r, e[2 * k].i, e[2 * k + 1].r, e[2 * k + 1].i);
+            __syncthreads();
+        }
+        nmr = 0;
+    }
 
     // 2. minimal residual on D_B
     for (int it = 0; it < nmr; ++it) {
@@ -750,13 +861,13 @@ __device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, c
     xx.store(i, e);
 }
 
-template <int LVB, class GA>
+template <bool JAC, int LVB, class GA>
 static int sap_run_h16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clover16 C, int nrhs, int n_cy, int n_mr,
                        int x_is_zero, cudaStream_t s, int compress)
 {
     const Geom &g = op->gauge->lat->g;
     constexpr size_t smem = h16_smem_bytes<LVB>();
-    auto kern = k_sap_h16<LVB, GA>;
+    auto kern = k_sap_h16<JAC, LVB, GA>;
     MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(g.nblocks / 2, nrhs);
     for (int cy = 0; cy < n_cy; ++cy)
@@ -770,15 +881,19 @@ static int sap_run_h16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clo
 }
 
 // FP16 storage: the compile-time kernel for cubic 2^4 and 4^4 domains
-template <class GA>
+template <bool JAC, class SP, class GA, class CL>
+static int sap_run_staged(const mgc_clover_s *op, SP b, SP x, GA U, CL C, int nrhs, int n_cy, int n_mr,
+                          int x_is_zero, cudaStream_t s, int prec, int compress);
+
+template <bool JAC, class GA>
 static int sap_dispatch16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clover16 C, int nrhs, int n_cy,
                           int n_mr, int x_is_zero, cudaStream_t s, int compress)
 {
     const Geom &g = op->gauge->lat->g;
     const bool cube = g.lb[0] == g.lb[1] && g.lb[1] == g.lb[2] && g.lb[2] == g.lb[3];
-    if (cube && g.lvb == 8) return sap_run_h16<8>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, compress);
-    if (cube && g.lvb == 4) return sap_run_h16<4>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, compress);
-    return sap_run_staged(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, 16, compress);
+    if (cube && g.lvb == 8) return sap_run_h16<JAC, 8>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, compress);
+    if (cube && g.lvb == 4) return sap_run_h16<JAC, 4>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, compress);
+    return sap_run_staged<JAC>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, 16, compress);
 }
 
 // ------------------------------------------------------------------ batches of lattices
@@ -822,7 +937,7 @@ __global__ void __launch_bounds__(1 << LVB, 2) k_sap_h16_batch(SapBatch<Spinor16
 {
     int k, jb, rr;
     batch_item(B, k, jb, rr);
-    sap_h16_body<LVB>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
+    sap_h16_body<false, LVB>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
 }
 
 // one block per SM: selecting the lattice at run time costs registers that a
@@ -832,7 +947,7 @@ __global__ void __launch_bounds__(256, 1) k_sap_staged_batch(SapBatch<SP, GA, CL
 {
     int k, jb, rr;
     batch_item(B, k, jb, rr);
-    sap_staged_body(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
+    sap_staged_body<false>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
 }
 
 template <class SP, class GA, class CL>
@@ -974,14 +1089,14 @@ int selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, cudaStr
     return h ? fail(MGC_ERR_TIMEOUT, "the self-test wait ran out as designed") : MGC_OK;
 }
 
-template <class SP, class GA, class CL>
+template <bool JAC, class SP, class GA, class CL>
 static int sap_run_staged(const mgc_clover_s *op, SP b, SP x, GA U, CL C, int nrhs, int n_cy, int n_mr,
                           int x_is_zero, cudaStream_t s, int prec, int compress)
 {
     const Geom &g = op->gauge->lat->g;
     const int vb = 1 << g.lvb;
     const size_t smem = staged_smem<GA, CL>(vb);
-    auto kern = k_sap_staged<SP, GA, CL>;
+    auto kern = k_sap_staged<JAC, SP, GA, CL>;
     MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(g.nblocks / 2, nrhs);
     for (int cy = 0; cy < n_cy; ++cy)
@@ -994,14 +1109,14 @@ static int sap_run_staged(const mgc_clover_s *op, SP b, SP x, GA U, CL C, int nr
     return MGC_OK;
 }
 
-template <class SP, class GA, class CL>
+template <bool JAC, class SP, class GA, class CL>
 static int sap_run(const Geom &g, SP b, SP x, GA U, CL C, double kappa, int nrhs, int n_cy, int n_mr, int x_is_zero,
                    cudaStream_t s, int prec, int compress)
 {
     using T = typename SP::Real;
     const int vb = 1 << g.lvb;
     const size_t smem = (size_t)vb * 12 * sizeof(Cx<T>) + 96 * sizeof(T);
-    auto kern = k_sap_colour<SP, GA, CL>;
+    auto kern = k_sap_colour<JAC, SP, GA, CL>;
     if (smem > 48 * 1024) MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(g.nblocks / 2, nrhs);
     for (int cy = 0; cy < n_cy; ++cy)
@@ -1014,34 +1129,52 @@ static int sap_run(const Geom &g, SP b, SP x, GA U, CL C, double kappa, int nrhs
     return MGC_OK;
 }
 
-int launch_sap(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_mr, int x_is_zero,
-               cudaStream_t s)
+// the smoother for D (JAC = false: clover C, MR) or for A = C^-1 D (JAC = true:
+// clover C^-1, Jacobi)
+template <bool JAC>
+static int sap_launch_impl(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_it,
+                           int x_is_zero, cudaStream_t s)
 {
     const mgc_gauge_s *ga = op->gauge;
     const Geom &g = ga->lat->g;
     if ((1 << g.lvb) > 256) return fail(MGC_ERR_UNSUPPORTED_SHAPE, "SAP domains are limited to 256 sites");
     if (prec == 64) {
-        return sap_run(g, Spinor64{(double2 *)b, g.lvb}, Spinor64{(double2 *)x, g.lvb}, Gauge64{ga->U64, g.lvb},
-                       Clover64{op->C64, g.lvb}, op->kappa, nrhs, n_cy, n_mr, x_is_zero, s, prec, ga->compress);
+        return sap_run<JAC>(g, Spinor64{(double2 *)b, g.lvb}, Spinor64{(double2 *)x, g.lvb}, Gauge64{ga->U64, g.lvb},
+                            Clover64{JAC ? op->Ci64 : op->C64, g.lvb}, op->kappa, nrhs, n_cy, n_it, x_is_zero, s, prec,
+                            ga->compress);
     }
     if (!has_prec(ga, prec)) return fail(MGC_ERR_INVALID_ARG, "no copy of the operator at this precision");
     const int cp = ga->compress;
     if (prec == 32) {
         Spinor32 B{(float4 *)b, g.lvb}, X{(float4 *)x, g.lvb};
-        Clover32 C{(float4 *)op->C32, g.lvb};
+        Clover32 C{(float4 *)(JAC ? op->Ci32 : op->C32), g.lvb};
         if (cp == 12)
-            return sap_run_staged(op, B, X, Gauge32x12{(float4 *)ga->U32, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s,
-                                  prec, cp);
-        return sap_run_staged(op, B, X, Gauge32x18{(float2 *)ga->U32, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s, prec,
-                              cp);
+            return sap_run_staged<JAC>(op, B, X, Gauge32x12{(float4 *)ga->U32, g.lvb}, C, nrhs, n_cy, n_it, x_is_zero,
+                                       s, prec, cp);
+        return sap_run_staged<JAC>(op, B, X, Gauge32x18{(float2 *)ga->U32, g.lvb}, C, nrhs, n_cy, n_it, x_is_zero, s,
+                                   prec, cp);
     }
     const size_t nV = (size_t)nrhs * g.V;
     Spinor16 B{(uint4 *)b, (float *)((uint4 *)b + nV * 3), g.lvb};
     Spinor16 X{(uint4 *)x, (float *)((uint4 *)x + nV * 3), g.lvb};
-    Clover16 C{(uint4 *)op->C16, op->C16_sc, g.lvb};
+    Clover16 C = JAC ? Clover16{(uint4 *)op->Ci16, op->Ci16_sc, g.lvb} : Clover16{(uint4 *)op->C16, op->C16_sc, g.lvb};
     if (cp == 12)
-        return sap_dispatch16(op, B, X, Gauge16x12{(uint2 *)ga->U16, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s, cp);
-    return sap_dispatch16(op, B, X, Gauge16x18{(uint32_t *)ga->U16, g.lvb}, C, nrhs, n_cy, n_mr, x_is_zero, s, cp);
+        return sap_dispatch16<JAC>(op, B, X, Gauge16x12{(uint2 *)ga->U16, g.lvb}, C, nrhs, n_cy, n_it, x_is_zero, s,
+                                   cp);
+    return sap_dispatch16<JAC>(op, B, X, Gauge16x18{(uint32_t *)ga->U16, g.lvb}, C, nrhs, n_cy, n_it, x_is_zero, s,
+                               cp);
+}
+
+int launch_sap(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_mr, int x_is_zero,
+               cudaStream_t s)
+{
+    return sap_launch_impl<false>(op, prec, b, x, nrhs, n_cy, n_mr, x_is_zero, s);
+}
+
+int launch_sap_A(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_jacobi,
+                 int x_is_zero, cudaStream_t s)
+{
+    return sap_launch_impl<true>(op, prec, b, x, nrhs, n_cy, n_jacobi, x_is_zero, s);
 }
 
 }  // namespace mgc

@@ -212,8 +212,8 @@ void free_work(mgc_clover_s *op)
 static int ensure_work(mgc_clover_s *op, int method, int m, int lowprec)
 {
     const Geom &g = op->gauge->lat->g;
-    const int m64 = (method == 2) ? 0 : (m < 4 ? 4 : m);
-    const int m32 = (method == 2) ? m : 0;
+    const int m64 = (method >= 2) ? 0 : (m < 4 ? 4 : m);
+    const int m32 = (method == 2) ? m : (method == 3 ? 4 : 0);
     SolverWork *W = op->work;
     if (W && W->m >= m64 && W->m32 >= m32 && (lowprec == 64 || lowprec == 32 || W->lowprec == lowprec)) return MGC_OK;
     const int keep64 = W ? W->m : 0, keep32 = W ? W->m32 : 0, keeplow = W ? W->lowprec : 0;
@@ -904,11 +904,208 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
     }
 }
 
+// ------------------------------------------------------------------ QWS solve
+// The paper's QWS solver (Sec. 2) for D x = b.  A = C^-1 D; the source of the
+// A-system is C^-1 r.  FP64 Richardson: r = b - D x (FP64), stop when
+// ||r|| <= tol ||b||; otherwise r_A = C^-1 r (FP64), solve (A M) y = r_A/||r_A||
+// with an FP32 BiCGStab to the inner tolerance, where M is the multiplicative
+// SAP for A with n_mr Jacobi iterations per domain (a fixed linear operator, so
+// plain BiCGStab applies) and A the FP32 operator; then x += ||r_A|| M y in
+// FP64.  BiCGStab scalars are FP64 host values; its inner products accumulate
+// as in the two-level solve.
+
+// z = M v for FP32 v, z (the SAP for A at the smoother precision)
+static int precondition32_A(mgc_clover_s *op, const mgc_solve_params *p, const float2 *v, float2 *z, cudaStream_t s)
+{
+    const Geom &g = op->gauge->lat->g;
+    SolverWork *W = op->work;
+    if (p->smoother_prec == 32) {
+        MGC_CUDA(cudaMemsetAsync(z, 0, spinor_bytes(g, 32, 1), s));
+        return launch_sap_A(op, 32, v, z, 1, p->n_cy, p->n_mr, 1, s);
+    }
+    MGC_TRY(launch_convert(g, 1, 32, v, 16, W->rl, s));
+    MGC_CUDA(cudaMemsetAsync(W->zl, 0, spinor_bytes(g, 16, 1), s));
+    MGC_TRY(launch_sap_A(op, 16, W->rl, W->zl, 1, p->n_cy, p->n_mr, 1, s));
+    return launch_convert(g, 1, 16, W->zl, 32, z, s);
+}
+
+// out = A M v (tmp receives M v)
+static int apply_AM(mgc_clover_s *op, const mgc_solve_params *p, const float2 *v, float2 *tmp, float2 *out,
+                    cudaStream_t s)
+{
+    MGC_TRY(precondition32_A(op, p, v, tmp, s));
+    return launch_apply_A(op, 32, tmp, out, 1, s);
+}
+
+__device__ __forceinline__ void facc_cdot(float *acc, float4 a, float4 b)
+{
+    facc_dot(acc, lo2(a), lo2(b));
+    facc_dot(acc, hi2(a), hi2(b));
+}
+
+// BiCGStab on (A M) y = r32 (unit norm) from y = 0 to ||residual|| <= tin;
+// y is left in W->z32[2]; *k_out counts iterations
+static int inner_bicgstab32(mgc_clover_s *op, const mgc_solve_params *p, double tin, int max_it, int *k_out,
+                            cudaStream_t s)
+{
+    SolverWork *W = op->work;
+    const long long n = (long long)op->gauge->lat->g.V * 12;
+    double *sc = W->scal;
+    float4 *rr = (float4 *)W->w32[0], *r0 = (float4 *)W->w32[1], *pv = (float4 *)W->w32[2];
+    float4 *v = (float4 *)W->w32[3], *sv = (float4 *)W->z32[0], *tv = (float4 *)W->z32[1];
+    float4 *y = (float4 *)W->z32[2];
+    float2 *tmp = W->z32[3];
+    const size_t vb = spinor_bytes(op->gauge->lat->g, 32, 1);
+    MGC_CUDA(cudaMemcpyAsync(rr, W->r32, vb, cudaMemcpyDeviceToDevice, s));
+    MGC_CUDA(cudaMemcpyAsync(r0, W->r32, vb, cudaMemcpyDeviceToDevice, s));
+    MGC_CUDA(cudaMemcpyAsync(pv, W->r32, vb, cudaMemcpyDeviceToDevice, s));
+    MGC_CUDA(cudaMemsetAsync(y, 0, vb, s));
+    double h[4];
+    MGC_TRY(reduce32<2>(n, [=] __device__(long long e, float *acc) { facc_cdot(acc, r0[e], rr[e]); }, W, sc + S_RHO, s,
+                        8.0 * n * 2));
+    MGC_TRY(read_scalars(W, S_RHO, 2, h, s));
+    zd rho(h[0], h[1]);
+    int k = 0;
+    while (k < max_it) {
+        MGC_TRY(apply_AM(op, p, (const float2 *)pv, tmp, (float2 *)v, s));
+        MGC_TRY(reduce32<2>(n, [=] __device__(long long e, float *acc) { facc_cdot(acc, r0[e], v[e]); }, W,
+                            sc + S_R0V, s, 8.0 * n * 2));
+        MGC_TRY(read_scalars(W, S_R0V, 2, h, s));
+        const zd r0v(h[0], h[1]);
+        if (bad(std::abs(r0v)) || r0v == zd(0, 0)) return fail(MGC_ERR_BREAKDOWN, "QWS BiCGStab: <r0, v> = 0");
+        const zd alpha = rho / r0v;
+        const float2 a = make_float2((float)alpha.real(), (float)alpha.imag());
+        MGC_TRY(map32(
+            n,
+            [=] __device__(long long e) {
+                float4 t4 = rr[e];
+                csub4(t4, a, v[e]);
+                sv[e] = t4;
+            },
+            s, 8.0 * n * 3));
+        MGC_TRY(apply_AM(op, p, (const float2 *)sv, tmp, (float2 *)tv, s));
+        MGC_TRY(reduce32<3>(
+            n,
+            [=] __device__(long long e, float *acc) {
+                const float4 t4 = tv[e];
+                facc_n2(acc, lo2(t4));
+                facc_n2(acc, hi2(t4));
+                facc_cdot(acc + 1, t4, sv[e]);
+            },
+            W, sc + S_TS, s, 8.0 * n * 2));
+        MGC_TRY(read_scalars(W, S_TS, 3, h, s));
+        const double tt = h[0];
+        const zd omega = tt > 0 ? zd(h[1], h[2]) / tt : zd(0, 0);
+        const float2 w = make_float2((float)omega.real(), (float)omega.imag());
+        // y += alpha p + omega s; r = s - omega t; ||r||^2 and <r0, r>
+        MGC_TRY(reduce32<3>(
+            n,
+            [=] __device__(long long e, float *acc) {
+                float4 yy = y[e];
+                const float4 s4 = sv[e];
+                csub4(yy, make_float2(-a.x, -a.y), pv[e]);
+                csub4(yy, make_float2(-w.x, -w.y), s4);
+                y[e] = yy;
+                float4 r4 = s4;
+                csub4(r4, w, tv[e]);
+                rr[e] = r4;
+                facc_n2(acc, lo2(r4));
+                facc_n2(acc, hi2(r4));
+                facc_cdot(acc + 1, r0[e], r4);
+            },
+            W, sc + S_TS, s, 8.0 * n * 7));
+        MGC_TRY(read_scalars(W, S_TS, 3, h, s));
+        ++k;
+        const double r2 = h[0];
+        if (bad(r2)) return fail(MGC_ERR_BREAKDOWN, "QWS BiCGStab: non-finite residual");
+        if (r2 <= tin * tin) break;
+        const zd rho1(h[1], h[2]);
+        if (rho == zd(0, 0) || omega == zd(0, 0)) break;
+        const zd beta = (rho1 / rho) * (alpha / omega);
+        const float2 bt = make_float2((float)beta.real(), (float)beta.imag());
+        MGC_TRY(map32(
+            n,
+            [=] __device__(long long e) {
+                float4 q = pv[e];
+                csub4(q, w, v[e]);  // p - omega v
+                float4 o = rr[e];
+                csub4(o, make_float2(-bt.x, -bt.y), q);  // r + beta (p - omega v)
+                pv[e] = o;
+            },
+            s, 8.0 * n * 3));
+        rho = rho1;
+    }
+    *k_out = k;
+    return MGC_OK;
+}
+
+static int qws(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
+{
+    SolverWork *W = op->work;
+    const Geom &g = op->gauge->lat->g;
+    const long long n = (long long)g.V * 12;
+    double2 *x = W->x, *r = W->r, *b = W->b, *t = W->t;
+    double *sc = W->scal;
+    double bb, rr;
+    MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, b[e]); }, W, sc + S_BB, s, 1));
+    MGC_TRY(read_scalar(W, S_BB, &bb, s));
+    info->iters = 0;
+    info->restarts = 0;
+    info->true_res = 0;
+    if (bb == 0.0) {
+        MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+        return MGC_OK;
+    }
+    if (p->x_is_guess) {
+        MGC_TRY(apply_D64(op, x, t, s));
+        MGC_TRY(residual(op, r, b, t, S_RR, s));
+        MGC_TRY(read_scalar(W, S_RR, &rr, s));
+    } else {
+        MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+        MGC_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        rr = bb;
+    }
+    const double tol2 = p->tol * p->tol * bb;
+    int iters = 0;
+    for (;;) {
+        info->true_res = std::sqrt(rr / bb);
+        if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "QWS Richardson: non-finite residual");
+        if (rr <= tol2) return MGC_OK;
+        if (iters >= p->max_iter) return MGC_NOT_CONVERGED;
+        // r_A = C^-1 r in FP64, its norm, and the unit-norm FP32 source
+        MGC_TRY(launch_clover_apply(op, 64, true, r, t, 1, s));
+        double ra2;
+        MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, t[e]); }, W, sc + S_NW, s, 1));
+        MGC_TRY(read_scalar(W, S_NW, &ra2, s));
+        if (bad(ra2) || ra2 == 0.0) return fail(MGC_ERR_BREAKDOWN, "QWS Richardson: zero or non-finite C^-1 r");
+        const double ra = std::sqrt(ra2);
+        MGC_TRY(launch_scale_to32(g, t, W->r32, 1.0 / ra, s));
+        double tin = p->inner_tol;
+        const double need = 0.5 * p->tol * std::sqrt(bb / rr);
+        if (need > tin) tin = need;
+        int k = 0;
+        MGC_TRY(inner_bicgstab32(op, p, tin, p->max_iter - iters, &k, s));
+        iters += k;
+        // x += ||r_A|| M y
+        float2 *e32 = W->z32[3];
+        MGC_TRY(precondition32_A(op, p, W->z32[2], e32, s));
+        MGC_TRY(launch_axpy_from32(g, x, e32, ra, 0.0, s));
+        MGC_TRY(apply_D64(op, x, t, s));
+        MGC_TRY(residual(op, r, b, t, S_RR, s));
+        MGC_TRY(read_scalar(W, S_RR, &rr, s));
+        info->iters = iters;
+        info->restarts++;
+        MGC_TRY(check_device_status(op, s));
+    }
+}
+
 // ------------------------------------------------------------------ entry points
 static int check_params(const mgc_clover_s *op, const mgc_solve_params *p)
 {
-    if (p->method < 0 || p->method > 2)
-        return fail(MGC_ERR_INVALID_ARG, "method must be 0 (FGCR), 1 (BiCGStab) or 2 (two-level)");
+    if (p->method < 0 || p->method > 3)
+        return fail(MGC_ERR_INVALID_ARG, "method must be 0 (FGCR), 1 (BiCGStab), 2 (two-level) or 3 (QWS)");
+    if (p->method == 3 && (p->precond != 1 || p->smoother_prec == 64 || !has_prec(op->gauge, 32)))
+        return fail(MGC_ERR_INVALID_ARG, "the QWS solve needs an FP32 copy, precond 1 and a 32- or 16-bit smoother");
     if (p->precond != 0 && p->precond != 1) return fail(MGC_ERR_INVALID_ARG, "precond must be 0 or 1");
     if (p->precond == 1 && !has_prec(op->gauge, p->smoother_prec))
         return fail(MGC_ERR_INVALID_ARG, "no copy of the operator at smoother_prec");
@@ -924,6 +1121,7 @@ static int run_method(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_inf
 {
     if (p->method == 0) return fgcr(op, p, info, s);
     if (p->method == 1) return fbicgstab(op, p, info, s);
+    if (p->method == 3) return qws(op, p, info, s);
     return two_level(op, p, info, s);
 }
 

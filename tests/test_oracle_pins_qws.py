@@ -126,3 +126,14 @@ def test_qws_solver_matches_dense_lu(fields):
     assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
     exact = np.linalg.solve(D, b.reshape(-1))
     assert np.linalg.norm(x.reshape(-1) - exact) <= 2e-10 * np.linalg.cond(D) * np.linalg.norm(exact)
+
+
+def test_jacobi_block_at_equals_jacobi_block(fields):
+    V, U, Cl, Ci = fields
+    bc = (1, 1, 0, 1)
+    VB = int(np.prod(BD))
+    r = synth.gaussian_spinor(BD, 76)
+    a = O.jacobi_block(DIMS, BD, bc, KAPPA, U, Cl, Ci, r, 4)
+    b = O.jacobi_block_at(DIMS, BD, bc, KAPPA, 1.0, U, r, 4)
+    assert np.array_equal(a, b)
+    assert a.shape == (VB, 4, 3)
