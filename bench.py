@@ -387,6 +387,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-force", action="store_true")
+    ap.add_argument("--no-qws", action="store_true")
     ap.add_argument("--profile-kernel", choices=["sap", "dslash"], default=None,
                     help="run only a few launches of one kernel on 24^3x48 (for ncu captures)")
     args = ap.parse_args()
@@ -547,6 +548,45 @@ def main():
         del op64, g64
     counters(lib, reset=True)
 
+    # ---------------- the paper's own QWS solve (method 3) on the same system
+    qws = None
+    if not args.no_qws:
+        pq = api.solve_params(method=3, precond=1, smoother_prec=w["prec"], n_cy=w["n_cy"], n_mr=w["n_mr"],
+                              tol=w["tol"], max_iter=500, inner_tol=w["inner_tol"])
+        xq, iq = op.solve(b, pq)
+        torch.cuda.synchronize()
+        counters(lib, reset=True)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        nq = 3
+        for _ in range(nq):
+            xq, iq = op.solve(b, pq)
+            if iq.status != 0 or iq.true_res > w["tol"]:
+                raise RuntimeError(f"QWS solve failed: status {iq.status}, residual {iq.true_res}")
+        q1.record(stream)
+        q1.synchronize()
+        nlq, nbq = counters(lib, reset=True)
+        t_q = q0.elapsed_time(q1) / 1e3 / nq
+        # one colour launch of the smoother for A (Jacobi, same storage)
+        zl.zero_()
+        op.sap_smooth_A(rl, zl, w["prec"], 1, 1, w["n_mr"], x_is_zero=True)
+        torch.cuda.synchronize()
+        sa = []
+        for _ in range(reps):
+            zl.zero_()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            op.sap_smooth_A(rl, zl, w["prec"], 1, w["n_cy"], w["n_mr"], x_is_zero=True)
+            a1.record(stream)
+            a1.synchronize()
+            sa.append(a0.elapsed_time(a1))
+        qws = {"method": "QWS (Sec. 2): FP64 Richardson around FP32 BiCGStab on A M_SAP, A = C^-1 D, "
+                         f"SAP for A with {w['n_mr']} Jacobi iterations per domain",
+               "ms": 1e3 * t_q, "bicgstab_iters": iq.iters, "true_residual": iq.true_res,
+               "gbs": nbq / nq / t_q / 1e9, "launches": nlq // nq,
+               "sap_A_launch_us": 1e3 * statistics.median(sa) / launches_per_call}
+        counters(lib, reset=True)
+
     # ---------------- batched workload and link force (reported beside the headline)
     batch = None if args.no_batch else bench_batch(lib, stream)
     force = None if args.no_force else bench_force(lib, stream)
@@ -610,6 +650,7 @@ def main():
         "e2e": {"value": nbytes_e2e / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": V * 192,
                 "d2h_bytes_per_step": V * 192, "ms_per_step": 1e3 * t_e2e / args.steps},
         "bytes_per_site_iteration": bytes_per_site_iter,
+        "qws_solve": qws,
         "batched": batch,
         "force": force,
     }
