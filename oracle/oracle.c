@@ -39,6 +39,11 @@
  *   - Sec. 2, QWS: the clover-preconditioned operator A = C^-1 D, its SAP
  *     with a fixed number of Jacobi iterations per block, and the QWS solver
  *     (Richardson around BiCGStab on A M_SAP, source multiplied by C^-1).
+ *   - Sec. 3, multigrid: aggregates split by chirality, block-orthonormal
+ *     null vectors as prolongation, R = P^dagger, D_c = R D P as a 9-point
+ *     coarse stencil, coarse BiCGStab, the two-level preconditioner (coarse
+ *     correction, then SAP post-smoothing), its setup from random vectors, and
+ *     the flexible-BiCGStab multigrid solve.
  *   - Sec. 3: the outer solver is flexible (the paper's is flexible BiCGStab);
  *     FGCR with restarts and flexible BiCGStab are provided, both right
  *     preconditioned with n_cy SAP sweeps from x = 0.
@@ -1004,6 +1009,402 @@ int or_solve(const int *L, const int *Bd, int tbc, double kappa, const cplx *U, 
     op_t op = {L, Bd, tbc, kappa, U, C, precond, ncy, nmr};
     if (method == 0) return fgcr(&op, b, x, m, tol, max_iter, iters, true_res);
     return fbicgstab(&op, b, x, tol, max_iter, iters, true_res);
+}
+
+/* ------------------------------------------------------------------ */
+/* two-level multigrid (Sec. 3)                                          */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Aggregates are blocks of Ad[0] x Ad[1] x Ad[2] x Ad[3] fine sites; the
+ * coarse lattice has Lc = L / Ad sites, indexed lexicographically (x fastest).
+ * Each aggregate is split by chirality (chi = 0: spins 0, 1, components 0..5;
+ * chi = 1: spins 2, 3, components 6..11), so a coarse site carries 2 nvec
+ * degrees of freedom, ordered (chi, i).  A coarse vector is u[a][chi][i].
+ * W holds nvec fine fields [i][site][12], orthonormal within every
+ * (aggregate, chirality): P u = sum_i W_i u(a(x), chi, i), R = P^dagger.
+ * The coarse operator D_c = R D P is stored as a 9-point stencil
+ * Dc[a][k][(chi', j)][(chi, i)], k = 0 for the coupling inside the aggregate
+ * (clover term and hops that stay inside), k = 1 + 2 mu for the fine hops from
+ * x + mu that cross the aggregate's +mu face, k = 2 + 2 mu for those from x - mu
+ * across its -mu face; (D_c u)(a) = sum_k Dc[a][k] u(a + offset_k).
+ */
+static void coarse_dims(const int *L, const int *Ad, int Lc[4])
+{
+    for (int mu = 0; mu < 4; ++mu) Lc[mu] = L[mu] / Ad[mu];
+}
+
+static long agg_of(long x, const int *L, const int *Ad)
+{
+    int c[4], Lc[4];
+    site_coords(x, L, c);
+    coarse_dims(L, Ad, Lc);
+    for (int mu = 0; mu < 4; ++mu) c[mu] /= Ad[mu];
+    return site_index(c, Lc);
+}
+
+/* coarse neighbour of a for stencil index k (k = 0: a itself) */
+static long coarse_nbr(long a, int k, const int *Lc)
+{
+    if (k == 0) return a;
+    int mu = (k - 1) / 2, dir = ((k - 1) % 2 == 0) ? +1 : -1, crossed;
+    return neighbour(a, mu, dir, Lc, &crossed);
+}
+
+/*
+ * Block modified Gram-Schmidt: for every aggregate and chirality, the
+ * restrictions of V_0 .. V_{nvec-1} are orthonormalised in order.  Returns the
+ * number of restrictions that were linearly dependent (zero after projection).
+ */
+int or_mg_basis(const int *L, const int *Ad, int nvec, const cplx *Vin, cplx *W)
+{
+    long V = vol4(L);
+    memcpy(W, Vin, sizeof(cplx) * nvec * V * 12);
+    int Lc[4];
+    coarse_dims(L, Ad, Lc);
+    long Vc = vol4(Lc), VA = V / Vc;
+    /* the sites of every aggregate, in increasing site order */
+    long *sites = malloc(sizeof(long) * V), *fill = calloc(Vc, sizeof(long));
+    for (long x = 0; x < V; ++x) {
+        long a = agg_of(x, L, Ad);
+        sites[a * VA + fill[a]++] = x;
+    }
+    int bad = 0;
+    for (long a = 0; a < Vc; ++a)
+        for (int chi = 0; chi < 2; ++chi)
+            for (int i = 0; i < nvec; ++i) {
+                cplx *wi = W + (long)i * V * 12;
+                const long *sa = sites + a * VA;
+                for (int j = 0; j < i; ++j) {
+                    const cplx *wj = W + (long)j * V * 12;
+                    cplx d = 0;
+                    for (long q = 0; q < VA; ++q)
+                        for (int c = 6 * chi; c < 6 * chi + 6; ++c) d += conj(wj[sa[q] * 12 + c]) * wi[sa[q] * 12 + c];
+                    for (long q = 0; q < VA; ++q)
+                        for (int c = 6 * chi; c < 6 * chi + 6; ++c) wi[sa[q] * 12 + c] -= d * wj[sa[q] * 12 + c];
+                }
+                double n2 = 0;
+                for (long q = 0; q < VA; ++q)
+                    for (int c = 6 * chi; c < 6 * chi + 6; ++c) {
+                        cplx z = wi[sa[q] * 12 + c];
+                        n2 += creal(z) * creal(z) + cimag(z) * cimag(z);
+                    }
+                if (n2 == 0) { ++bad; continue; }
+                double inv = 1.0 / sqrt(n2);
+                for (long q = 0; q < VA; ++q)
+                    for (int c = 6 * chi; c < 6 * chi + 6; ++c) wi[sa[q] * 12 + c] *= inv;
+            }
+    free(sites);
+    free(fill);
+    return bad;
+}
+
+/* u = R v = P^dagger v */
+void or_mg_restrict(const int *L, const int *Ad, int nvec, const cplx *W, const cplx *v, cplx *u)
+{
+    long V = vol4(L);
+    int Lc[4];
+    coarse_dims(L, Ad, Lc);
+    long nc = vol4(Lc) * 2 * nvec;
+    for (long k = 0; k < nc; ++k) u[k] = 0;
+    for (long x = 0; x < V; ++x) {
+        long a = agg_of(x, L, Ad);
+        for (int chi = 0; chi < 2; ++chi)
+            for (int i = 0; i < nvec; ++i) {
+                const cplx *wi = W + (long)i * V * 12;
+                cplx d = 0;
+                for (int c = 6 * chi; c < 6 * chi + 6; ++c) d += conj(wi[x * 12 + c]) * v[x * 12 + c];
+                u[(a * 2 + chi) * nvec + i] += d;
+            }
+    }
+}
+
+/* v = P u */
+void or_mg_prolong(const int *L, const int *Ad, int nvec, const cplx *W, const cplx *u, cplx *v)
+{
+    long V = vol4(L);
+    for (long x = 0; x < V; ++x) {
+        long a = agg_of(x, L, Ad);
+        for (int c = 0; c < 12; ++c) {
+            int chi = c / 6;
+            cplx acc = 0;
+            for (int i = 0; i < nvec; ++i) acc += W[(long)i * V * 12 + x * 12 + c] * u[(a * 2 + chi) * nvec + i];
+            v[x * 12 + c] = acc;
+        }
+    }
+}
+
+/* the hop term of D at x from its neighbour in direction dir (+1/-1) along mu:
+ * -kappa s (1 -/+ gamma_mu) U psi(y), s the boundary sign (out is overwritten) */
+static void hop_term(const int *L, int tbc, double kappa, const cplx *U, long x, int mu, int dir, const cplx *psi_y,
+                     cplx out[12])
+{
+    init_gamma();
+    int crossed;
+    long y = neighbour(x, mu, dir, L, &crossed);
+    double sg = (mu == 3 && crossed) ? (double)tbc : 1.0;
+    cplx v[4][3];
+    if (dir > 0) colour_apply(link_ptr(U, x, mu), 0, psi_y, v);
+    else colour_apply(link_ptr(U, y, mu), 1, psi_y, v);
+    for (int i = 0; i < 12; ++i) out[i] = 0;
+    add_hop(out, mu, dir > 0 ? -1.0 : +1.0, kappa * sg, v);
+}
+
+/* Dc = R D P, assembled per fine site and hop direction (layout above) */
+void or_mg_coarse_op(const int *L, const int *Ad, int tbc, double kappa, const cplx *U, const cplx *C, int nvec,
+                     const cplx *W, cplx *Dc)
+{
+    long V = vol4(L);
+    int Lc[4];
+    coarse_dims(L, Ad, Lc);
+    long Vc = vol4(Lc);
+    const int N2 = 2 * nvec;
+    memset(Dc, 0, sizeof(cplx) * Vc * 9 * N2 * N2);
+    for (long x = 0; x < V; ++x) {
+        long a = agg_of(x, L, Ad);
+        int c[4];
+        site_coords(x, L, c);
+        for (int k = 0; k < 9; ++k) {
+            /* the pieces of D at x that belong to stencil entry k */
+            for (int chi = 0; chi < 2; ++chi)
+                for (int i = 0; i < nvec; ++i) {
+                    const cplx *wi = W + (long)i * V * 12;
+                    cplx h[12] = {0};
+                    if (k == 0) {
+                        /* clover term, then the hops that stay inside the aggregate */
+                        cplx p[12];
+                        for (int q = 0; q < 12; ++q) p[q] = (q / 6 == chi) ? wi[x * 12 + q] : 0;
+                        for (int r = 0; r < 12; ++r)
+                            for (int q = 0; q < 12; ++q) h[r] += C[x * 144 + r * 12 + q] * p[q];
+                        for (int mu = 0; mu < 4; ++mu)
+                            for (int dir = -1; dir <= 1; dir += 2) {
+                                int inside = (dir > 0) ? ((c[mu] + 1) % Ad[mu] != 0) : (c[mu] % Ad[mu] != 0);
+                                if (!inside) continue;
+                                int crossed;
+                                long y = neighbour(x, mu, dir, L, &crossed);
+                                for (int q = 0; q < 12; ++q) p[q] = (q / 6 == chi) ? wi[y * 12 + q] : 0;
+                                cplx t[12];
+                                hop_term(L, tbc, kappa, U, x, mu, dir, p, t);
+                                for (int r = 0; r < 12; ++r) h[r] += t[r];
+                            }
+                    } else {
+                        int mu = (k - 1) / 2, dir = ((k - 1) % 2 == 0) ? +1 : -1;
+                        int across = (dir > 0) ? ((c[mu] + 1) % Ad[mu] == 0) : (c[mu] % Ad[mu] == 0);
+                        if (!across) continue;
+                        int crossed;
+                        long y = neighbour(x, mu, dir, L, &crossed);
+                        cplx p[12];
+                        for (int q = 0; q < 12; ++q) p[q] = (q / 6 == chi) ? wi[y * 12 + q] : 0;
+                        hop_term(L, tbc, kappa, U, x, mu, dir, p, h);
+                    }
+                    for (int chp = 0; chp < 2; ++chp)
+                        for (int j = 0; j < nvec; ++j) {
+                            const cplx *wj = W + (long)j * V * 12;
+                            cplx d = 0;
+                            for (int q = 6 * chp; q < 6 * chp + 6; ++q) d += conj(wj[x * 12 + q]) * h[q];
+                            Dc[((a * 9 + k) * N2 + chp * nvec + j) * N2 + chi * nvec + i] += d;
+                        }
+                }
+        }
+    }
+}
+
+void or_mg_coarse_apply(const int *L, const int *Ad, int nvec, const cplx *Dc, const cplx *u, cplx *out)
+{
+    int Lc[4];
+    coarse_dims(L, Ad, Lc);
+    long Vc = vol4(Lc);
+    const int N2 = 2 * nvec;
+    for (long a = 0; a < Vc; ++a)
+        for (int r = 0; r < N2; ++r) {
+            cplx acc = 0;
+            for (int k = 0; k < 9; ++k) {
+                long b = coarse_nbr(a, k, Lc);
+                for (int q = 0; q < N2; ++q) acc += Dc[((a * 9 + k) * N2 + r) * N2 + q] * u[b * N2 + q];
+            }
+            out[a * N2 + r] = acc;
+        }
+}
+
+/* BiCGStab on D_c x = b from x = 0 to ||r|| <= tol ||b|| or maxit iterations */
+int or_mg_coarse_solve(const int *L, const int *Ad, int nvec, const cplx *Dc, const cplx *b, cplx *x, double tol,
+                       int maxit, int *iters_out)
+{
+    int Lc[4];
+    coarse_dims(L, Ad, Lc);
+    long n = vol4(Lc) * 2 * nvec;
+    cplx *r = malloc(sizeof(cplx) * n), *r0 = malloc(sizeof(cplx) * n), *p = malloc(sizeof(cplx) * n);
+    cplx *v = malloc(sizeof(cplx) * n), *s = malloc(sizeof(cplx) * n), *t = malloc(sizeof(cplx) * n);
+    double bn = sqrt(vnorm2(n, b));
+    int it = 0, status = 1;
+    for (long i = 0; i < n; ++i) { x[i] = 0; r[i] = b[i]; r0[i] = b[i]; p[i] = b[i]; }
+    if (bn == 0) { status = 0; goto done; }
+    cplx rho = vdot(n, r0, r);
+    while (it < maxit) {
+        or_mg_coarse_apply(L, Ad, nvec, Dc, p, v);
+        cplx r0v = vdot(n, r0, v);
+        if (r0v == 0) break;
+        cplx alpha = rho / r0v;
+        for (long i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+        or_mg_coarse_apply(L, Ad, nvec, Dc, s, t);
+        double tt = vnorm2(n, t);
+        cplx omega = (tt > 0) ? vdot(n, t, s) / tt : 0;
+        for (long i = 0; i < n; ++i) {
+            x[i] += alpha * p[i] + omega * s[i];
+            r[i] = s[i] - omega * t[i];
+        }
+        ++it;
+        if (sqrt(vnorm2(n, r)) <= tol * bn) { status = 0; break; }
+        cplx rho1 = vdot(n, r0, r);
+        if (rho == 0 || omega == 0) break;
+        cplx beta = (rho1 / rho) * (alpha / omega);
+        for (long i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        rho = rho1;
+    }
+done:
+    *iters_out = it;
+    free(r); free(r0); free(p); free(v); free(s); free(t);
+    return status;
+}
+
+typedef struct {
+    const int *L, *Bd, *Ad;
+    int tbc;
+    double kappa;
+    const cplx *U, *C, *Ci;
+    int nvec;
+    const cplx *W, *Dc;
+    int ncy, nj;     /* post-smoother: n_cy sweeps of the SAP for A, nj Jacobi iterations */
+    double ctol;     /* coarse BiCGStab tolerance and iteration limit */
+    int cmaxit;
+} mg_t;
+
+/*
+ * One application of the two-level preconditioner to v: the coarse-grid
+ * correction x = P D_c^-1 R v (D_c^-1 by BiCGStab to ctol), then the
+ * post-smoother x += M_SAP(C^-1 (v - D x)) with QWS's M_SAP for A (Sec. 3).
+ */
+static void mg_apply(const mg_t *m, const cplx *v, cplx *x)
+{
+    long V = vol4(m->L), n = V * 12;
+    int Lc[4];
+    coarse_dims(m->L, m->Ad, Lc);
+    long nc = vol4(Lc) * 2 * m->nvec;
+    cplx *u = malloc(sizeof(cplx) * nc), *cx = malloc(sizeof(cplx) * nc);
+    cplx *r = malloc(sizeof(cplx) * n), *ra = malloc(sizeof(cplx) * n), *e = malloc(sizeof(cplx) * n);
+    int it;
+    or_mg_restrict(m->L, m->Ad, m->nvec, m->W, v, u);
+    or_mg_coarse_solve(m->L, m->Ad, m->nvec, m->Dc, u, cx, m->ctol, m->cmaxit, &it);
+    or_mg_prolong(m->L, m->Ad, m->nvec, m->W, cx, x);
+    or_dirac(m->L, m->tbc, m->kappa, m->U, m->C, x, r, 0);
+    for (long i = 0; i < n; ++i) r[i] = v[i] - r[i];
+    clover_inv_apply(V, m->Ci, r, ra);
+    for (long i = 0; i < n; ++i) e[i] = 0;
+    or_sap_A(m->L, m->Bd, m->tbc, m->kappa, m->U, m->C, m->Ci, ra, e, m->ncy, m->nj);
+    for (long i = 0; i < n; ++i) x[i] += e[i];
+    free(u); free(cx); free(r); free(ra); free(e);
+}
+
+void or_mg_precond(const int *L, const int *Bd, const int *Ad, int tbc, double kappa, const cplx *U, const cplx *C,
+                   const cplx *Ci, int nvec, const cplx *W, const cplx *Dc, int ncy, int nj, double ctol, int cmaxit,
+                   const cplx *v, cplx *x)
+{
+    mg_t m = {L, Bd, Ad, tbc, kappa, U, C, Ci, nvec, W, Dc, ncy, nj, ctol, cmaxit};
+    mg_apply(&m, v, x);
+}
+
+/*
+ * Setup (Sec. 3): the initial null vectors are M_SAP applied to nvec random
+ * vectors eta (given), V_i = M_SAP(C^-1 eta_i); W and D_c are built from them;
+ * then n_adapt times every V_i is replaced by the two-level preconditioner
+ * (with the current W, D_c) applied to it, and W, D_c are rebuilt.  Returns
+ * the number of linearly dependent aggregate restrictions met.
+ */
+int or_mg_setup(const int *L, const int *Bd, const int *Ad, int tbc, double kappa, const cplx *U, const cplx *C,
+                const cplx *Ci, int nvec, const cplx *eta, int ncy, int nj, int n_adapt, double ctol, int cmaxit,
+                cplx *W, cplx *Dc)
+{
+    long V = vol4(L), n = V * 12;
+    cplx *Vv = malloc(sizeof(cplx) * nvec * n), *ra = malloc(sizeof(cplx) * n);
+    for (int i = 0; i < nvec; ++i) {
+        clover_inv_apply(V, Ci, eta + (long)i * n, ra);
+        cplx *vi = Vv + (long)i * n;
+        for (long k = 0; k < n; ++k) vi[k] = 0;
+        or_sap_A(L, Bd, tbc, kappa, U, C, Ci, ra, vi, ncy, nj);
+    }
+    int bad = or_mg_basis(L, Ad, nvec, Vv, W);
+    or_mg_coarse_op(L, Ad, tbc, kappa, U, C, nvec, W, Dc);
+    mg_t m = {L, Bd, Ad, tbc, kappa, U, C, Ci, nvec, W, Dc, ncy, nj, ctol, cmaxit};
+    cplx *t = malloc(sizeof(cplx) * n);
+    for (int pass = 0; pass < n_adapt; ++pass) {
+        for (int i = 0; i < nvec; ++i) {
+            mg_apply(&m, Vv + (long)i * n, t);
+            memcpy(Vv + (long)i * n, t, sizeof(cplx) * n);
+        }
+        bad += or_mg_basis(L, Ad, nvec, Vv, W);
+        or_mg_coarse_op(L, Ad, tbc, kappa, U, C, nvec, W, Dc);
+    }
+    free(t); free(Vv); free(ra);
+    return bad;
+}
+
+/*
+ * The multigrid solve of D x = b (Sec. 3): flexible BiCGStab (the outer solver
+ * of the paper) with the two-level preconditioner, from x = 0, stopping when
+ * the true residual ||b - D x|| <= tol ||b||.  Returns 0 when converged.
+ */
+int or_solve_mg(const int *L, const int *Bd, const int *Ad, int tbc, double kappa, const cplx *U, const cplx *C,
+                const cplx *Ci, int nvec, const cplx *W, const cplx *Dc, int ncy, int nj, double ctol, int cmaxit,
+                const cplx *b, cplx *x, double tol, int max_iter, int *iters_out, double *res_out)
+{
+    mg_t m = {L, Bd, Ad, tbc, kappa, U, C, Ci, nvec, W, Dc, ncy, nj, ctol, cmaxit};
+    long n = vol4(L) * 12;
+    cplx *r = malloc(sizeof(cplx) * n), *r0 = malloc(sizeof(cplx) * n);
+    cplx *p = malloc(sizeof(cplx) * n), *ph = malloc(sizeof(cplx) * n);
+    cplx *v = malloc(sizeof(cplx) * n), *s = malloc(sizeof(cplx) * n);
+    cplx *sh = malloc(sizeof(cplx) * n), *t = malloc(sizeof(cplx) * n);
+    cplx *tmp = malloc(sizeof(cplx) * n);
+    double bnorm = sqrt(vnorm2(n, b));
+    int iters = 0, status = 1;
+    double rel = 0;
+    for (long i = 0; i < n; ++i) x[i] = 0;
+    if (bnorm == 0) { status = 0; goto done; }
+    for (;;) {
+        or_dirac(L, tbc, kappa, U, C, x, tmp, 0);
+        for (long i = 0; i < n; ++i) { r[i] = b[i] - tmp[i]; r0[i] = r[i]; p[i] = r[i]; }
+        rel = sqrt(vnorm2(n, r)) / bnorm;
+        if (rel <= tol) { status = 0; break; }
+        if (iters >= max_iter) break;
+        cplx rho = vdot(n, r0, r);
+        while (iters < max_iter) {
+            mg_apply(&m, p, ph);
+            or_dirac(L, tbc, kappa, U, C, ph, v, 0);
+            cplx r0v = vdot(n, r0, v);
+            if (r0v == 0) break;
+            cplx alpha = rho / r0v;
+            for (long i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+            mg_apply(&m, s, sh);
+            or_dirac(L, tbc, kappa, U, C, sh, t, 0);
+            double tt = vnorm2(n, t);
+            cplx omega = (tt > 0) ? vdot(n, t, s) / tt : 0;
+            for (long i = 0; i < n; ++i) {
+                x[i] += alpha * ph[i] + omega * sh[i];
+                r[i] = s[i] - omega * t[i];
+            }
+            ++iters;
+            if (sqrt(vnorm2(n, r)) <= tol * bnorm) break;
+            cplx rho1 = vdot(n, r0, r);
+            if (rho == 0 || omega == 0) break;
+            cplx beta = (rho1 / rho) * (alpha / omega);
+            for (long i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+            rho = rho1;
+        }
+    }
+done:
+    *iters_out = iters;
+    *res_out = rel;
+    free(r); free(r0); free(p); free(ph); free(v); free(s); free(sh); free(t); free(tmp);
+    return status;
 }
 
 /* ------------------------------------------------------------------ */

@@ -62,6 +62,24 @@ def lib():
                                    C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int),
                                    C.POINTER(C.c_double)]
         L.or_solve_qws.restype = C.c_int
+        L.or_mg_basis.argtypes = [_i4, _i4, C.c_int, _c16, _c16]
+        L.or_mg_basis.restype = C.c_int
+        L.or_mg_restrict.argtypes = [_i4, _i4, C.c_int, _c16, _c16, _c16]
+        L.or_mg_prolong.argtypes = [_i4, _i4, C.c_int, _c16, _c16, _c16]
+        L.or_mg_coarse_op.argtypes = [_i4, _i4, C.c_int, C.c_double, _c16, _c16, C.c_int, _c16, _c16]
+        L.or_mg_coarse_apply.argtypes = [_i4, _i4, C.c_int, _c16, _c16, _c16]
+        L.or_mg_coarse_solve.argtypes = [_i4, _i4, C.c_int, _c16, _c16, _c16, C.c_double, C.c_int,
+                                         C.POINTER(C.c_int)]
+        L.or_mg_coarse_solve.restype = C.c_int
+        L.or_mg_precond.argtypes = [_i4, _i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, C.c_int, _c16, _c16,
+                                    C.c_int, C.c_int, C.c_double, C.c_int, _c16, _c16]
+        L.or_mg_setup.argtypes = [_i4, _i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, C.c_int, _c16, C.c_int,
+                                  C.c_int, C.c_int, C.c_double, C.c_int, _c16, _c16]
+        L.or_mg_setup.restype = C.c_int
+        L.or_solve_mg.argtypes = [_i4, _i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, C.c_int, _c16, _c16,
+                                  C.c_int, C.c_int, C.c_double, C.c_int, _c16, _c16, C.c_double, C.c_int,
+                                  C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.or_solve_mg.restype = C.c_int
         _lib = L
     return _lib
 
@@ -298,6 +316,118 @@ def solve_qws(dims, bdims, tbc, kappa, U, Cl, Ci, b, ncy=4, nj=4, tol=1e-10, inn
     st = lib().or_solve_qws(_dims(dims), _dims(bdims), int(tbc), float(kappa), _sized(U, V * 36, "U"),
                             _sized(Cl, V * 144, "Cl"), _sized(Ci, V * 144, "Ci"), b, x, int(ncy), int(nj),
                             float(tol), float(inner_tol), int(max_iter), C.byref(it), C.byref(res))
+    return x, int(st), int(it.value), float(res.value)
+
+
+# ---------------------------------------------------------------- multigrid (Sec. 3)
+# W: (nvec, V, 4, 3) block-orthonormal null vectors; coarse vectors u: (Vc, 2, nvec);
+# coarse operator Dc: (Vc, 9, 2 nvec, 2 nvec), stencil order self, +x, -x, +y, -y, +z, -z, +t, -t.
+
+def coarse_volume(dims, agg):
+    return int(np.prod([int(d) // int(a) for d, a in zip(dims, agg)]))
+
+
+def mg_basis(dims, agg, Vin):
+    """Block modified Gram-Schmidt per (aggregate, chirality).  Returns (W, n_dependent)."""
+    Vin = _c(Vin)
+    nvec = Vin.shape[0]
+    _sized(Vin, nvec * _vol(dims) * 12, "V")
+    W = np.zeros_like(Vin)
+    bad = lib().or_mg_basis(_dims(dims), _dims(agg), nvec, Vin, W)
+    return W, int(bad)
+
+
+def mg_restrict(dims, agg, W, v):
+    W = _c(W)
+    nvec = W.shape[0]
+    u = np.zeros((coarse_volume(dims, agg), 2, nvec), np.complex128)
+    lib().or_mg_restrict(_dims(dims), _dims(agg), nvec, _sized(W, nvec * _vol(dims) * 12, "W"),
+                         _sized(v, _vol(dims) * 12, "v"), u)
+    return u
+
+
+def mg_prolong(dims, agg, W, u):
+    W = _c(W)
+    nvec = W.shape[0]
+    v = np.zeros((_vol(dims), 4, 3), np.complex128)
+    lib().or_mg_prolong(_dims(dims), _dims(agg), nvec, _sized(W, nvec * _vol(dims) * 12, "W"),
+                        _sized(u, coarse_volume(dims, agg) * 2 * nvec, "u"), v)
+    return v
+
+
+def mg_coarse_op(dims, agg, tbc, kappa, U, Cl, W):
+    W = _c(W)
+    nvec = W.shape[0]
+    V = _vol(dims)
+    Dc = np.zeros((coarse_volume(dims, agg), 9, 2 * nvec, 2 * nvec), np.complex128)
+    lib().or_mg_coarse_op(_dims(dims), _dims(agg), int(tbc), float(kappa), _sized(U, V * 36, "U"),
+                          _sized(Cl, V * 144, "Cl"), nvec, _sized(W, nvec * V * 12, "W"), Dc)
+    return Dc
+
+
+def mg_coarse_apply(dims, agg, Dc, u):
+    Dc = _c(Dc)
+    nvec = Dc.shape[-1] // 2
+    Vc = coarse_volume(dims, agg)
+    out = np.zeros((Vc, 2, nvec), np.complex128)
+    lib().or_mg_coarse_apply(_dims(dims), _dims(agg), nvec, _sized(Dc, Vc * 9 * 4 * nvec * nvec, "Dc"),
+                             _sized(u, Vc * 2 * nvec, "u"), out)
+    return out
+
+
+def mg_coarse_solve(dims, agg, Dc, b, tol=1e-10, maxit=1000):
+    Dc = _c(Dc)
+    nvec = Dc.shape[-1] // 2
+    Vc = coarse_volume(dims, agg)
+    x = np.zeros((Vc, 2, nvec), np.complex128)
+    it = C.c_int(0)
+    st = lib().or_mg_coarse_solve(_dims(dims), _dims(agg), nvec, _sized(Dc, Vc * 9 * 4 * nvec * nvec, "Dc"),
+                                  _sized(b, Vc * 2 * nvec, "b"), x, float(tol), int(maxit), C.byref(it))
+    return x, int(st), int(it.value)
+
+
+def mg_precond(dims, bdims, agg, tbc, kappa, U, Cl, Ci, W, Dc, v, ncy=2, nj=4, ctol=1e-2, cmaxit=100):
+    """The two-level preconditioner applied to v: coarse correction, then SAP post-smoothing."""
+    W = _c(W)
+    nvec = W.shape[0]
+    V = _vol(dims)
+    x = np.zeros((V, 4, 3), np.complex128)
+    lib().or_mg_precond(_dims(dims), _dims(bdims), _dims(agg), int(tbc), float(kappa), _sized(U, V * 36, "U"),
+                        _sized(Cl, V * 144, "Cl"), _sized(Ci, V * 144, "Ci"), nvec, _sized(W, nvec * V * 12, "W"),
+                        _sized(Dc, coarse_volume(dims, agg) * 36 * nvec * nvec, "Dc"), int(ncy), int(nj),
+                        float(ctol), int(cmaxit), _sized(v, V * 12, "v"), x)
+    return x
+
+
+def mg_setup(dims, bdims, agg, tbc, kappa, U, Cl, Ci, eta, ncy=2, nj=4, n_adapt=4, ctol=1e-2, cmaxit=100):
+    """Null vectors from M_SAP on the random vectors eta, then n_adapt adaptive passes.
+    Returns (W, Dc, n_dependent)."""
+    eta = _c(eta)
+    nvec = eta.shape[0]
+    V = _vol(dims)
+    W = np.zeros((nvec, V, 4, 3), np.complex128)
+    Dc = np.zeros((coarse_volume(dims, agg), 9, 2 * nvec, 2 * nvec), np.complex128)
+    bad = lib().or_mg_setup(_dims(dims), _dims(bdims), _dims(agg), int(tbc), float(kappa), _sized(U, V * 36, "U"),
+                            _sized(Cl, V * 144, "Cl"), _sized(Ci, V * 144, "Ci"), nvec,
+                            _sized(eta, nvec * V * 12, "eta"), int(ncy), int(nj), int(n_adapt), float(ctol),
+                            int(cmaxit), W, Dc)
+    return W, Dc, int(bad)
+
+
+def solve_mg(dims, bdims, agg, tbc, kappa, U, Cl, Ci, W, Dc, b, ncy=2, nj=4, ctol=1e-2, cmaxit=100, tol=1e-10,
+             max_iter=500):
+    """Flexible BiCGStab with the two-level preconditioner.  Returns (x, status, iterations, true residual)."""
+    W = _c(W)
+    nvec = W.shape[0]
+    V = _vol(dims)
+    x = np.zeros((V, 4, 3), np.complex128)
+    it = C.c_int(0)
+    res = C.c_double(0)
+    st = lib().or_solve_mg(_dims(dims), _dims(bdims), _dims(agg), int(tbc), float(kappa), _sized(U, V * 36, "U"),
+                           _sized(Cl, V * 144, "Cl"), _sized(Ci, V * 144, "Ci"), nvec, _sized(W, nvec * V * 12, "W"),
+                           _sized(Dc, coarse_volume(dims, agg) * 36 * nvec * nvec, "Dc"), int(ncy), int(nj),
+                           float(ctol), int(cmaxit), _sized(b, V * 12, "b"), x, float(tol), int(max_iter),
+                           C.byref(it), C.byref(res))
     return x, int(st), int(it.value), float(res.value)
 
 
