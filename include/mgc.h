@@ -283,6 +283,72 @@ int mgc_force(mgc_clover_t op, const double *phi, double *dSdU, const mgc_solve_
               mgc_solve_info *info, double *action, void *stream);
 
 /*
+ * Two-level multigrid (Sec. 3), single precision inside the preconditioner.
+ * Aggregates are agg[0] x agg[1] x agg[2] x agg[3] fine sites (each extent a
+ * multiple of the SAP domain extent and dividing the lattice), split by
+ * chirality (spins 0, 1 and spins 2, 3), so a coarse site carries 2 nvec
+ * degrees of freedom (1 <= nvec <= MGC_MG_MAX_NVEC).  The prolongation P is the
+ * nvec null vectors orthonormalised per aggregate and chirality (modified
+ * Gram-Schmidt in vector order), the restriction is R = P^dagger and the
+ * coarse operator D_c = R D P, stored as a 9-point stencil (the coupling inside
+ * an aggregate and the fine hops across each of its 8 faces).  The
+ * preconditioner applied to v is the coarse correction x = P D_c^-1 R v
+ * (D_c^-1 by BiCGStab to coarse_tol or coarse_maxit iterations) followed by
+ * n_cy sweeps of QWS's SAP for A on C^-1 (v - D x) (post-smoothing), all in
+ * FP32 arithmetic.  The handle needs an operator with an FP32 copy; it does not
+ * own the operator (destroy it first).
+ *
+ * Canonical coarse vectors are complex128 [Vc][chirality 2][nvec] with the
+ * coarse sites lexicographic (x fastest) on the lattice dims / agg; the coarse
+ * stencil export is complex128 [Vc][9][2 nvec][2 nvec] (row, column) with the
+ * stencil order: inside, +x, -x, +y, -y, +z, -z, +t, -t, entry k applied to
+ * the coarse neighbour in that direction.
+ */
+#define MGC_MG_MAX_NVEC 32
+typedef struct mgc_mg_s *mgc_mg_t;
+typedef struct {
+    int n_cy;          /* post-smoother sweeps */
+    int n_jacobi;      /* Jacobi iterations per domain in the post-smoother */
+    int smoother_prec; /* 32 or 16 */
+    double coarse_tol; /* relative residual of the coarse BiCGStab */
+    int coarse_maxit;
+    int n_adapt;       /* adaptive setup passes */
+} mgc_mg_params;
+void mgc_mg_params_default(mgc_mg_params *p);
+int mgc_mg_create(mgc_clover_t op, const int agg[4], int nvec, mgc_mg_t *out);
+int mgc_mg_destroy(mgc_mg_t mg);
+/* coarse lattice volume */
+long long mgc_mg_coarse_volume(mgc_mg_t mg);
+/*
+ * Setup (Sec. 3): null vectors V_i = M_SAP(C^-1 eta_i) from the nvec random
+ * fields eta (canonical complex128 [nvec][V][4][3], device; the caller draws
+ * them), then W and D_c; then n_adapt passes that replace every V_i by the
+ * preconditioner applied to it (scaled to unit norm) and rebuild W and D_c.
+ * Synchronises stream.
+ */
+int mgc_mg_setup(mgc_mg_t mg, const double *eta, const mgc_mg_params *p, void *stream);
+/* W and D_c from given vectors V (canonical, device) without any smoothing */
+int mgc_mg_set_vectors(mgc_mg_t mg, const double *V, void *stream);
+/* W (canonical [nvec][V][4][3]) and D_c (layout above), both complex128 on the device */
+int mgc_mg_export(mgc_mg_t mg, double *W, double *Dc, void *stream);
+/* u = R v, v = P u, out = D_c u, all canonical complex128 on the device, computed in FP32 */
+int mgc_mg_restrict(mgc_mg_t mg, const double *v, double *u, void *stream);
+int mgc_mg_prolong(mgc_mg_t mg, const double *u, double *v, void *stream);
+int mgc_mg_coarse_apply(mgc_mg_t mg, const double *u, double *out, void *stream);
+/* D_c x = b by BiCGStab to tol (relative) or maxit iterations; *iters receives the count.  Synchronises. */
+int mgc_mg_coarse_solve(mgc_mg_t mg, const double *b, double *x, double tol, int maxit, int *iters, void *stream);
+/* x = the two-level preconditioner applied to v (canonical fine fields, device).  Synchronises. */
+int mgc_mg_precond(mgc_mg_t mg, const double *v, double *x, const mgc_mg_params *p, void *stream);
+/*
+ * The multigrid solve (Sec. 3): flexible BiCGStab with FP64 vectors and the
+ * FP64 operator, preconditioned by the two-level preconditioner, to the true
+ * residual tol.  b, x canonical complex128 (one field; p->on_device as in
+ * mgc_solve; p->tol and p->max_iter are used).  Synchronises.
+ */
+int mgc_mg_solve(mgc_mg_t mg, const double *b, double *x, const mgc_solve_params *p, const mgc_mg_params *mp,
+                 mgc_solve_info *info, void *stream);
+
+/*
  * Batches of lattices (no paper counterpart; the paper's multiple
  * right-hand sides, Sec. 4, extended to several lattices at once).  A batch
  * groups up to MGC_BATCH_MAX operators that share storage precision, link

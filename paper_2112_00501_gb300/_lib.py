@@ -38,6 +38,17 @@ class SolveParams(C.Structure):
     ]
 
 
+class MgParams(C.Structure):
+    _fields_ = [
+        ("n_cy", C.c_int),
+        ("n_jacobi", C.c_int),
+        ("smoother_prec", C.c_int),
+        ("coarse_tol", C.c_double),
+        ("coarse_maxit", C.c_int),
+        ("n_adapt", C.c_int),
+    ]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [
         ("status", C.c_int),
@@ -80,6 +91,19 @@ SIGNATURES = {
     "mgc_solve": (_I, [_P, _P, _P, _I, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P]),
     "mgc_force": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(SolveInfo), C.POINTER(_D), _P]),
     "mgc_solve_noalloc": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P]),
+    "mgc_mg_params_default": (None, [C.POINTER(MgParams)]),
+    "mgc_mg_create": (_I, [_P, C.POINTER(_I), _I, C.POINTER(_P)]),
+    "mgc_mg_destroy": (_I, [_P]),
+    "mgc_mg_coarse_volume": (C.c_longlong, [_P]),
+    "mgc_mg_setup": (_I, [_P, _P, C.POINTER(MgParams), _P]),
+    "mgc_mg_set_vectors": (_I, [_P, _P, _P]),
+    "mgc_mg_export": (_I, [_P, _P, _P, _P]),
+    "mgc_mg_restrict": (_I, [_P, _P, _P, _P]),
+    "mgc_mg_prolong": (_I, [_P, _P, _P, _P]),
+    "mgc_mg_coarse_apply": (_I, [_P, _P, _P, _P]),
+    "mgc_mg_coarse_solve": (_I, [_P, _P, _P, _D, _I, C.POINTER(_I), _P]),
+    "mgc_mg_precond": (_I, [_P, _P, _P, C.POINTER(MgParams), _P]),
+    "mgc_mg_solve": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(MgParams), C.POINTER(SolveInfo), _P]),
     "mgc_batch_create": (_I, [C.POINTER(_P), C.POINTER(_I), _I, C.POINTER(_P)]),
     "mgc_batch_destroy": (_I, [_P]),
     "mgc_batch_systems": (_I, [_P]),

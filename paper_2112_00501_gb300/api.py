@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import SolveInfo, SolveParams, check
+from ._lib import MgParams, SolveInfo, SolveParams, check
 
 
 def _stream(stream=None):
@@ -365,3 +365,109 @@ class Batch:
         if st not in (_lib.MGC_OK, _lib.MGC_NOT_CONVERGED):
             check(st, "mgc_batch_solve")
         return xs, list(infos)
+
+
+def mg_params(**kw) -> MgParams:
+    p = MgParams()
+    _lib.load().mgc_mg_params_default(C.byref(p))
+    names = {f[0] for f in MgParams._fields_}
+    for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown multigrid parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class Multigrid:
+    """Two-level multigrid on one operator (the ABI's mgc_mg_t): aggregates of
+    agg sites split by chirality, nvec null vectors.  Canonical fields are
+    complex128 torch tensors on the GPU: fine (V, 4, 3), coarse (Vc, 2, nvec)."""
+
+    def __init__(self, op: CloverOperator, agg, nvec: int):
+        self.lib = op.lib
+        self.op = op
+        self.agg = tuple(int(a) for a in agg)
+        self.nvec = int(nvec)
+        h = C.c_void_p()
+        check(self.lib.mgc_mg_create(op.handle, (C.c_int * 4)(*self.agg), self.nvec, C.byref(h)), "mgc_mg_create")
+        self.handle = h
+        self.coarse_volume = int(self.lib.mgc_mg_coarse_volume(h))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self.lib.mgc_mg_destroy(h)
+            self.handle = None
+
+    def _fine(self, v):
+        return _canon(v, "cuda").reshape(self.op.lattice.volume, 4, 3)
+
+    def _coarse(self, u):
+        return _canon(u, "cuda").reshape(self.coarse_volume, 2, self.nvec)
+
+    def setup(self, eta, params: MgParams | None = None, stream=None, **kw):
+        p = params if params is not None else mg_params(**kw)
+        e = _canon(eta, "cuda").reshape(self.nvec, self.op.lattice.volume, 4, 3)
+        check(self.lib.mgc_mg_setup(self.handle, _ptr(e), C.byref(p), _stream(stream)), "mgc_mg_setup")
+
+    def set_vectors(self, V, stream=None):
+        v = _canon(V, "cuda").reshape(self.nvec, self.op.lattice.volume, 4, 3)
+        check(self.lib.mgc_mg_set_vectors(self.handle, _ptr(v), _stream(stream)), "mgc_mg_set_vectors")
+
+    def export(self, stream=None):
+        W = torch.empty((self.nvec, self.op.lattice.volume, 4, 3), dtype=torch.complex128, device="cuda")
+        n2 = 2 * self.nvec
+        Dc = torch.empty((self.coarse_volume, 9, n2, n2), dtype=torch.complex128, device="cuda")
+        check(self.lib.mgc_mg_export(self.handle, _ptr(W), _ptr(Dc), _stream(stream)), "mgc_mg_export")
+        return W, Dc
+
+    def restrict(self, v, stream=None):
+        u = torch.empty((self.coarse_volume, 2, self.nvec), dtype=torch.complex128, device="cuda")
+        check(self.lib.mgc_mg_restrict(self.handle, _ptr(self._fine(v)), _ptr(u), _stream(stream)), "mgc_mg_restrict")
+        return u
+
+    def prolong(self, u, stream=None):
+        v = torch.empty((self.op.lattice.volume, 4, 3), dtype=torch.complex128, device="cuda")
+        check(self.lib.mgc_mg_prolong(self.handle, _ptr(self._coarse(u)), _ptr(v), _stream(stream)), "mgc_mg_prolong")
+        return v
+
+    def coarse_apply(self, u, stream=None):
+        out = torch.empty((self.coarse_volume, 2, self.nvec), dtype=torch.complex128, device="cuda")
+        check(self.lib.mgc_mg_coarse_apply(self.handle, _ptr(self._coarse(u)), _ptr(out), _stream(stream)),
+              "mgc_mg_coarse_apply")
+        return out
+
+    def coarse_solve(self, b, tol=1e-6, maxit=1000, stream=None):
+        x = torch.empty((self.coarse_volume, 2, self.nvec), dtype=torch.complex128, device="cuda")
+        it = C.c_int(0)
+        check(self.lib.mgc_mg_coarse_solve(self.handle, _ptr(self._coarse(b)), _ptr(x), float(tol), int(maxit),
+                                           C.byref(it), _stream(stream)), "mgc_mg_coarse_solve")
+        return x, int(it.value)
+
+    def precond(self, v, params: MgParams | None = None, stream=None, **kw):
+        p = params if params is not None else mg_params(**kw)
+        x = torch.empty((self.op.lattice.volume, 4, 3), dtype=torch.complex128, device="cuda")
+        check(self.lib.mgc_mg_precond(self.handle, _ptr(self._fine(v)), _ptr(x), C.byref(p), _stream(stream)),
+              "mgc_mg_precond")
+        return x
+
+    def solve(self, b, params: SolveParams | None = None, mg: MgParams | None = None, out=None, stream=None,
+              **kw):
+        """Flexible BiCGStab preconditioned by the two-level preconditioner.  Returns (x, info)."""
+        p = params if params is not None else solve_params(**kw)
+        m = mg if mg is not None else mg_params()
+        host = not (isinstance(b, torch.Tensor) and b.is_cuda)
+        bt = _canon(b, "cpu" if host else "cuda")
+        if host and not bt.is_pinned():
+            bt = bt.pin_memory()
+        p.on_device = 0 if host else 1
+        p.x_is_guess = 0
+        x = out if out is not None else torch.zeros_like(bt)
+        if host and out is None:
+            x = x.pin_memory()
+        info = SolveInfo()
+        st = self.lib.mgc_mg_solve(self.handle, _ptr(bt), _ptr(x), C.byref(p), C.byref(m), C.byref(info),
+                                   _stream(stream))
+        if st not in (_lib.MGC_OK, _lib.MGC_NOT_CONVERGED):
+            check(st, "mgc_mg_solve")
+        return x, info

@@ -156,6 +156,17 @@ int launch_scale_to32_batch(const BatchSpec &spec, const size_t *off, const doub
 int launch_axpy_from32_batch(const BatchSpec &spec, const size_t *off, double2 *x, const float2 *e,
                              const double *scal, const int *flag, cudaStream_t s);
 
+// multigrid (mg.cu; the outer solve in solver.cu)
+}  // namespace mgc
+struct mgc_mg_s;
+namespace mgc {
+// z = the two-level preconditioner applied to v (FP64 packed; vnorm = ||v||)
+int mg_precond64(mgc_mg_s *M, const mgc_mg_params *p, const double2 *v, double2 *z, double vnorm, cudaStream_t s);
+mgc_clover_s *mg_operator(mgc_mg_s *M);
+// flexible BiCGStab with the two-level preconditioner (canonical b, x)
+int mg_solve(mgc_mg_s *M, const double *b, double *x, const mgc_solve_params *p, const mgc_mg_params *mp,
+             mgc_solve_info *info, cudaStream_t s);
+
 // force.cu
 int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_params *p, mgc_solve_info *info,
           double *action, cudaStream_t s);

@@ -424,7 +424,23 @@ static int fgcr(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *inf
 }
 
 // ------------------------------------------------------------------ flexible BiCGStab
-static int fbicgstab(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
+// preconditioners for fbicgstab_impl: z = M v, returning a status
+struct PreSAP {
+    mgc_clover_s *op;
+    const mgc_solve_params *p;
+    cudaStream_t s;
+    int operator()(const double2 *v, double2 *z) const { return precondition(op, p, v, z, s); }
+};
+static int mg_precondition(mgc_mg_s *M, const mgc_mg_params *mp, const double2 *v, double2 *z, cudaStream_t s);
+struct PreMG {
+    mgc_mg_s *M;
+    const mgc_mg_params *mp;
+    cudaStream_t s;
+    int operator()(const double2 *v, double2 *z) const { return mg_precondition(M, mp, v, z, s); }
+};
+
+template <class PRE>
+static int fbicgstab_impl(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s, PRE pre)
 {
     SolverWork *W = op->work;
     const long long n = (long long)op->gauge->lat->g.V * 12;
@@ -466,7 +482,7 @@ static int fbicgstab(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
         }
         bool restart = false;
         while (iters < p->max_iter) {
-            MGC_TRY(precondition(op, p, pv, ph, s));
+            MGC_TRY(pre(pv, ph));
             MGC_TRY(apply_D64(op, ph, v, s));
             MGC_TRY(reduce<2>(n, [=] __device__(long long e, double *acc) { acc_dot(acc, r0[e], v[e]); }, W, sc + S_R0V, s, 2));
             // s = r - alpha v
@@ -477,7 +493,7 @@ static int fbicgstab(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
                     sv[e] = csub(r[e], cmul(alpha, v[e]));
                 },
                 s, 3));
-            MGC_TRY(precondition(op, p, sv, sh, s));
+            MGC_TRY(pre(sv, sh));
             MGC_TRY(apply_D64(op, sh, t, s));
             MGC_TRY(reduce<3>(
                 n,
@@ -540,6 +556,61 @@ static int fbicgstab(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
         (void)restart;
         info->restarts++;
     }
+}
+
+static int fbicgstab(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
+{
+    return fbicgstab_impl(op, p, info, s, PreSAP{op, p, s});
+}
+
+// ------------------------------------------------------------------ multigrid solve (Sec. 3)
+// flexible BiCGStab with FP64 vectors and operator, preconditioned by the
+// two-level preconditioner (FP32 inside; it takes v / ||v||)
+static int mg_precondition(mgc_mg_s *M, const mgc_mg_params *mp, const double2 *v, double2 *z, cudaStream_t s)
+{
+    mgc_clover_s *op = mg_operator(M);
+    SolverWork *W = op->work;
+    const long long n = (long long)op->gauge->lat->g.V * 12;
+    MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, v[e]); }, W, W->scal + S_NW, s, 1));
+    double nn;
+    MGC_TRY(read_scalar(W, S_NW, &nn, s));
+    if (bad(nn)) return fail(MGC_ERR_BREAKDOWN, "multigrid: non-finite vector");
+    return mg_precond64(M, mp, v, z, std::sqrt(nn), s);
+}
+
+int mg_solve(mgc_mg_s *M, const double *b, double *x, const mgc_solve_params *p, const mgc_mg_params *mp,
+             mgc_solve_info *info, cudaStream_t s)
+{
+    mgc_clover_s *op = mg_operator(M);
+    if (!(p->tol > 0) || p->max_iter < 1) return fail(MGC_ERR_INVALID_ARG, "tol or max_iter out of range");
+    MGC_TRY(ensure_work(op, 1, 4, 64));
+    SolverWork *W = op->work;
+    const Geom &g = op->gauge->lat->g;
+    const size_t vb = spinor_bytes(g, 64, 1);
+    if (p->on_device) {
+        MGC_TRY(launch_pack(g, 64, 1, b, W->b, s));
+        if (p->x_is_guess) MGC_TRY(launch_pack(g, 64, 1, x, W->x, s));
+    } else {
+        MGC_CUDA(cudaMemcpyAsync(W->stage, b, vb, cudaMemcpyHostToDevice, s));
+        MGC_TRY(launch_pack(g, 64, 1, (const double *)W->stage, W->b, s));
+        if (p->x_is_guess) {
+            MGC_CUDA(cudaMemcpyAsync(W->stage, x, vb, cudaMemcpyHostToDevice, s));
+            MGC_TRY(launch_pack(g, 64, 1, (const double *)W->stage, W->x, s));
+        }
+    }
+    *info = mgc_solve_info{MGC_OK, 0, 0, 0.0};
+    const int st = fbicgstab_impl(op, p, info, s, PreMG{M, mp, s});
+    info->status = st;
+    if (st != MGC_OK && st != MGC_NOT_CONVERGED) return st;
+    if (p->on_device) {
+        MGC_TRY(launch_unpack(g, 64, 1, W->x, x, s));
+    } else {
+        MGC_TRY(launch_unpack(g, 64, 1, W->x, (double *)W->stage, s));
+        MGC_CUDA(cudaMemcpyAsync(x, W->stage, vb, cudaMemcpyDeviceToHost, s));
+    }
+    MGC_CUDA(cudaStreamSynchronize(s));
+    MGC_TRY(check_device_status(op, s));
+    return st;
 }
 
 // ------------------------------------------------------------------ two-level solve

@@ -1,0 +1,162 @@
+"""GPU parity of the two-level multigrid (Sec. 3) against the FP64 oracle,
+through the C ABI.  Both sides build their null-vector basis and coarse
+operator from the same synthetic vectors; the GPU works in FP32 (the paper's
+single-precision multigrid), so pieces are compared at the FP32 tolerance,
+iterative pieces through their residuals, and the multigrid solve through the
+oracle's true residual."""
+import numpy as np
+import pytest
+
+from helpers import TOL, fields, rel
+from oracle import oracle as O
+from paper_2112_00501_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# (lattice name or dims, SAP block, aggregate)
+GEOMS = {
+    "4^4/2^4": ((4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)),
+    "4^4/4x2x2x4": ((4, 4, 4, 4), (2, 2, 2, 2), (4, 2, 2, 4)),
+    "4x4x4x8/2^4": ((4, 4, 4, 8), (2, 2, 2, 2), (2, 2, 2, 2)),
+    "8^4/4^4": ((8, 8, 8, 8), (4, 4, 4, 4), (4, 4, 4, 4)),
+}
+KAPPA, CSW, EPS = 0.1355, 1.0, 0.4
+
+_cache = {}
+
+
+def _setup(geom, prec=32, compress=18):
+    from paper_2112_00501_gb300 import api
+
+    dims, block, agg = GEOMS[geom]
+    key = (geom, prec, compress)
+    if key not in _cache:
+        U = synth.gauge_field(dims, EPS, synth.gauge_seed(40))
+        Cl = O.clover(dims, KAPPA, CSW, U)
+        Ci = O.clover_inverse(dims, Cl)
+        lat = api.Lattice(dims, block, -1)
+        op = api.CloverOperator(api.Gauge(lat, torch.from_numpy(U).cuda(), storage_prec=prec, compress=compress),
+                                KAPPA, CSW)
+        _cache[key] = (dims, block, agg, U, Cl, Ci, lat, op)
+    return _cache[key]
+
+
+@pytest.mark.parametrize("nvec", [3, 10])
+@pytest.mark.parametrize("geom", list(GEOMS))
+def test_basis_transfer_and_coarse_operator(geom, nvec):
+    from paper_2112_00501_gb300 import api
+
+    dims, block, agg, U, Cl, Ci, lat, op = _setup(geom)
+    V = synth.gaussian_spinor(dims, 41, nrhs=nvec)
+    mg = api.Multigrid(op, agg, nvec)
+    mg.set_vectors(torch.from_numpy(V).cuda())
+    W, Dc = mg.export()
+    Wo, bad = O.mg_basis(dims, agg, V)
+    assert bad == 0
+    Dco = O.mg_coarse_op(dims, agg, -1, KAPPA, U, Cl, Wo)
+    assert rel(W.cpu().numpy(), Wo) < TOL[32]
+    assert rel(Dc.cpu().numpy(), Dco) < TOL[32]
+    v = synth.gaussian_spinor(dims, 42)
+    Vc = O.coarse_volume(dims, agg)
+    g = synth.rng(43)
+    u = g.normal(size=(Vc, 2, nvec)) + 1j * g.normal(size=(Vc, 2, nvec))
+    assert rel(mg.restrict(torch.from_numpy(v).cuda()).cpu().numpy(), O.mg_restrict(dims, agg, Wo, v)) < TOL[32]
+    assert rel(mg.prolong(torch.from_numpy(u).cuda()).cpu().numpy(), O.mg_prolong(dims, agg, Wo, u)) < TOL[32]
+    assert rel(mg.coarse_apply(torch.from_numpy(u).cuda()).cpu().numpy(),
+               O.mg_coarse_apply(dims, agg, Dco, u)) < TOL[32]
+
+
+def test_coarse_solve_residual():
+    from paper_2112_00501_gb300 import api
+
+    geom = "8^4/4^4"
+    dims, block, agg, U, Cl, Ci, lat, op = _setup(geom)
+    nvec = 4
+    V = synth.gaussian_spinor(dims, 44, nrhs=nvec)
+    mg = api.Multigrid(op, agg, nvec)
+    mg.set_vectors(torch.from_numpy(V).cuda())
+    Wo, _ = O.mg_basis(dims, agg, V)
+    Dco = O.mg_coarse_op(dims, agg, -1, KAPPA, U, Cl, Wo)
+    Vc = O.coarse_volume(dims, agg)
+    g = synth.rng(45)
+    b = g.normal(size=(Vc, 2, nvec)) + 1j * g.normal(size=(Vc, 2, nvec))
+    x, it = mg.coarse_solve(torch.from_numpy(b).cuda(), tol=1e-6, maxit=2000)
+    assert 0 < it < 2000
+    r = b - O.mg_coarse_apply(dims, agg, Dco, x.cpu().numpy())
+    assert np.linalg.norm(r) <= 1e-5 * np.linalg.norm(b)
+    xo, st, _ = O.mg_coarse_solve(dims, agg, Dco, b, tol=1e-12, maxit=5000)
+    assert st == 0 and rel(x.cpu().numpy(), xo) < 1e-4
+
+
+@pytest.mark.parametrize("smoother", [32, 16])
+def test_preconditioner_matches_oracle(smoother):
+    from paper_2112_00501_gb300 import api
+
+    geom = "8^4/4^4"
+    dims, block, agg, U, Cl, Ci, lat, op = _setup(geom, prec=smoother, compress=12 if smoother == 16 else 18)
+    nvec = 4
+    V = synth.gaussian_spinor(dims, 46, nrhs=nvec)
+    mg = api.Multigrid(op, agg, nvec)
+    mg.set_vectors(torch.from_numpy(V).cuda())
+    Wo, _ = O.mg_basis(dims, agg, V)
+    Dco = O.mg_coarse_op(dims, agg, -1, KAPPA, U, Cl, Wo)
+    v = synth.gaussian_spinor(dims, 47)
+    got = mg.precond(torch.from_numpy(v).cuda(), n_cy=2, n_jacobi=3, smoother_prec=smoother, coarse_tol=1e-7,
+                     coarse_maxit=4000).cpu().numpy()
+    want = O.mg_precond(dims, block, agg, -1, KAPPA, U, Cl, Ci, Wo, Dco, v, ncy=2, nj=3, ctol=1e-12, cmaxit=10000)
+    assert rel(got, want) < (1e-4 if smoother == 32 else TOL[16])
+
+
+def test_setup_without_adaptive_pass_matches_oracle():
+    from paper_2112_00501_gb300 import api
+
+    geom = "8^4/4^4"
+    dims, block, agg, U, Cl, Ci, lat, op = _setup(geom)
+    nvec = 4
+    eta = synth.gaussian_spinor(dims, 48, nrhs=nvec)
+    mg = api.Multigrid(op, agg, nvec)
+    mg.setup(torch.from_numpy(eta).cuda(), n_cy=2, n_jacobi=3, n_adapt=0)
+    W, Dc = mg.export()
+    Wo, Dco, bad = O.mg_setup(dims, block, agg, -1, KAPPA, U, Cl, Ci, eta, ncy=2, nj=3, n_adapt=0)
+    assert bad == 0
+    assert rel(W.cpu().numpy(), Wo) < TOL[32]
+    assert rel(Dc.cpu().numpy(), Dco) < TOL[32]
+
+
+@pytest.mark.parametrize("smoother", [32, 16])
+def test_multigrid_solve_reaches_1e10(smoother):
+    from paper_2112_00501_gb300 import api
+
+    geom = "8^4/4^4"
+    dims, block, agg, U, Cl, Ci, lat, op = _setup(geom, prec=smoother, compress=12 if smoother == 16 else 18)
+    nvec = 8
+    eta = synth.gaussian_spinor(dims, 49, nrhs=nvec)
+    mg = api.Multigrid(op, agg, nvec)
+    mp = api.mg_params(n_cy=2, n_jacobi=4, smoother_prec=smoother, n_adapt=2)
+    mg.setup(torch.from_numpy(eta).cuda(), mp)
+    b = synth.gaussian_spinor(dims, synth.source_seed(40))
+    x, info = mg.solve(torch.from_numpy(b).cuda(), mg=mp, tol=1e-10, max_iter=200)
+    assert info.status == 0 and info.true_res <= 1e-10
+    r = b - O.dirac(dims, -1, KAPPA, U, Cl, x.cpu().numpy())
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
+    # host pointers give the same solution path
+    xh, ih = mg.solve(b, mg=mp, tol=1e-10, max_iter=200)
+    assert ih.status == 0 and not xh.is_cuda
+
+
+def test_multigrid_rejects_bad_shapes():
+    from paper_2112_00501_gb300 import api
+    from paper_2112_00501_gb300._lib import MgcError
+
+    dims, block, agg, U, Cl, Ci, lat, op = _setup("8^4/4^4")
+    with pytest.raises(MgcError) as e:
+        api.Multigrid(op, (2, 4, 4, 4), 4)  # smaller than a SAP domain
+    assert e.value.status == 2
+    with pytest.raises(MgcError):
+        api.Multigrid(op, (4, 4, 4, 4), 0)
+    lat64 = api.Lattice(dims, block, -1)
+    op64 = api.CloverOperator(api.Gauge(lat64, torch.from_numpy(U).cuda(), storage_prec=64), KAPPA, CSW)
+    with pytest.raises(MgcError):
+        api.Multigrid(op64, (4, 4, 4, 4), 4)
