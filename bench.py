@@ -211,6 +211,8 @@ BYTES_PER_SITE_ITER_DEFAULT = 4836.0
 BATCH_WORKLOAD = dict(lattices=[((24, 24, 24, 48), 12), ((16, 16, 16, 16), 8), ((8, 8, 8, 8), 8)],
                       block=(4, 4, 4, 4), eps=0.4, kappa=0.1355, csw=1.0, config_index=3, prec=32, compress=18,
                       n_cy=4, n_mr=4, restart=16, tol=1e-10, inner_tol=2e-6)
+# two-level multigrid on the bench system: the paper's 8x4x4x4 aggregates and 16 null vectors
+MG_AGG, MG_NVEC, MG_RHS = (8, 4, 4, 4), 16, 12
 # link force workload
 FORCE_WORKLOAD = dict(dims=(24, 24, 24, 48), block=(4, 4, 4, 4), eps=0.4, kappa=0.1355, csw=1.0, config_index=4,
                       prec=32, compress=18)
@@ -316,6 +318,70 @@ def bench_batch(lib, stream):
     return out
 
 
+def bench_mg(lib, stream, op, b, params, w):
+    """The two-level multigrid on the bench system: setup (M_SAP on random
+    vectors, 4 adaptive passes), one solve to 1e-10, and MG_RHS solves on the
+    same setup against MG_RHS solves of the bench's own method."""
+    import torch
+
+    from paper_2112_00501_gb300 import api
+
+    V = op.lattice.volume
+    gen = torch.Generator(device="cuda").manual_seed(5000)
+    eta = torch.complex(torch.randn((MG_NVEC, V, 4, 3), generator=gen, device="cuda", dtype=torch.float64),
+                        torch.randn((MG_NVEC, V, 4, 3), generator=gen, device="cuda", dtype=torch.float64))
+    eta = eta * (0.5 ** 0.5)
+    mg = api.Multigrid(op, MG_AGG, MG_NVEC)
+    mp = api.mg_params(n_cy=2, n_jacobi=4, smoother_prec=w["prec"], coarse_tol=5e-2, coarse_maxit=100, n_adapt=4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mg.setup(eta, mp)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    del eta
+    ps = api.solve_params(tol=w["tol"], max_iter=500)
+    x, info = mg.solve(b, ps, mp)
+    if info.status != 0 or info.true_res > w["tol"]:
+        raise RuntimeError(f"multigrid solve failed: status {info.status}, residual {info.true_res}")
+    torch.cuda.synchronize()
+    counters(lib, reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    x, info = mg.solve(b, ps, mp)
+    e1.record(stream)
+    e1.synchronize()
+    t_solve = e0.elapsed_time(e1) / 1e3
+    nl, nb = counters(lib, reset=True)
+    # MG_RHS equations on one configuration (sources: the bench source rotated by a site shift)
+    srcs = [torch.roll(b, shifts=k * 97, dims=0) for k in range(MG_RHS)]
+    e0.record(stream)
+    for q in srcs:
+        _, iq = mg.solve(q, ps, mp)
+        if iq.status != 0:
+            raise RuntimeError("multigrid solve failed")
+    e1.record(stream)
+    e1.synchronize()
+    t_mg12 = e0.elapsed_time(e1) / 1e3
+    e0.record(stream)
+    for q in srcs:
+        _, iq = op.solve(q, params)
+        if iq.status != 0:
+            raise RuntimeError("two-level solve failed")
+    e1.record(stream)
+    e1.synchronize()
+    t_tl12 = e0.elapsed_time(e1) / 1e3
+    counters(lib, reset=True)
+    del mg
+    return {"method": f"flexible BiCGStab (FP64) with the two-level preconditioner: {MG_NVEC} null vectors, "
+                      f"{'x'.join(map(str, MG_AGG))} aggregates split by chirality, coarse BiCGStab to "
+                      f"{mp.coarse_tol:g}, post-smoother {mp.n_cy} SAP-for-A sweeps x {mp.n_jacobi} Jacobi, "
+                      f"setup with {mp.n_adapt} adaptive passes",
+            "setup_s": t_setup, "solve_ms": 1e3 * t_solve, "outer_iters": info.iters, "true_residual": info.true_res,
+            "solve_launches": nl, "solve_gbs": nb / t_solve / 1e9,
+            f"{MG_RHS}_equations": {"mg_setup_plus_solves_s": t_setup + t_mg12, "mg_solves_s": t_mg12,
+                                   "two_level_solves_s": t_tl12}}
+
+
 def bench_force(lib, stream):
     """dS/dU for S = phi^+ (D^+ D)^-1 phi on 24^3 x 48 (two solves and the
     force kernels)."""
@@ -388,6 +454,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-force", action="store_true")
     ap.add_argument("--no-qws", action="store_true")
+    ap.add_argument("--no-mg", action="store_true")
     ap.add_argument("--profile-kernel", choices=["sap", "dslash"], default=None,
                     help="run only a few launches of one kernel on 24^3x48 (for ncu captures)")
     args = ap.parse_args()
@@ -588,6 +655,7 @@ def main():
         counters(lib, reset=True)
 
     # ---------------- batched workload and link force (reported beside the headline)
+    mgres = None if args.no_mg else bench_mg(lib, stream, op, b, params, w)
     batch = None if args.no_batch else bench_batch(lib, stream)
     force = None if args.no_force else bench_force(lib, stream)
     counters(lib, reset=True)
@@ -651,6 +719,7 @@ def main():
                 "d2h_bytes_per_step": V * 192, "ms_per_step": 1e3 * t_e2e / args.steps},
         "bytes_per_site_iteration": bytes_per_site_iter,
         "qws_solve": qws,
+        "multigrid": mgres,
         "batched": batch,
         "force": force,
     }
