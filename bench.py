@@ -346,10 +346,12 @@ def bench_mg(lib, stream, op, b, params, w):
     torch.cuda.synchronize()
     counters(lib, reset=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("mg_solve")
     e0.record(stream)
     x, info = mg.solve(b, ps, mp)
     e1.record(stream)
     e1.synchronize()
+    torch.cuda.nvtx.range_pop()
     t_solve = e0.elapsed_time(e1) / 1e3
     nl, nb = counters(lib, reset=True)
     # MG_RHS equations on one configuration (sources: the bench source rotated by a site shift)

@@ -12,7 +12,6 @@
 // consecutive rows).  Reductions of coarse vectors run in FP64 with a fixed
 // grid and a fixed-order second pass.
 #include <cmath>
-#include <complex>
 #include <type_traits>
 #include <vector>
 
@@ -27,7 +26,6 @@ constexpr int CHUNK = 8;    // null vectors per restriction pass
 constexpr int CRT = 256;    // threads of the coarse reductions
 constexpr int CRG = 64;     // blocks of the coarse reductions
 
-typedef std::complex<double> zd;
 
 struct MgGeom {
     Geom g;          // fine lattice
@@ -393,6 +391,27 @@ __global__ void __launch_bounds__(CRT) k_creduce(int n, F f, double *partial)
         }
 }
 
+// device-side BiCGStab scalars of the coarse solve (FP64):
+// rho, <r0, v>, ||t||^2, <t, s>, ||r||^2, <r0, r_new>
+enum { CS_RHO = 0, CS_R0V = 2, CS_TT = 4, CS_TS = 5, CS_RR = 7, CS_RHO1 = 8, CS_N = 10 };
+__device__ __forceinline__ double2 ldz(const double *p) { return make_double2(p[0], p[1]); }
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b)
+{
+    const double n = b.x * b.x + b.y * b.y;
+    return n > 0 ? make_double2((a.x * b.x + a.y * b.y) / n, (a.y * b.x - a.x * b.y) / n) : make_double2(0, 0);
+}
+__device__ __forceinline__ double2 zmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 tof(double2 a) { return make_float2((float)a.x, (float)a.y); }
+// alpha = rho / <r0, v>; omega = <t, s> / ||t||^2
+__device__ __forceinline__ double2 cs_alpha(const double *sc) { return zdiv(ldz(sc + CS_RHO), ldz(sc + CS_R0V)); }
+__device__ __forceinline__ double2 cs_omega(const double *sc)
+{
+    return sc[CS_TT] > 0 ? make_double2(sc[CS_TS] / sc[CS_TT], sc[CS_TS + 1] / sc[CS_TT]) : make_double2(0, 0);
+}
+
 template <int NV>
 __global__ void k_cfinish(const double *partial, double *out)
 {
@@ -525,10 +544,10 @@ int read_scalars(mgc_mg_s *M, int nd, double *out, cudaStream_t s)
 }
 
 template <int NV, class F>
-int creduce(mgc_mg_s *M, F f, cudaStream_t s)
+int creduce(mgc_mg_s *M, F f, cudaStream_t s, int slot = 0)
 {
     k_creduce<NV><<<CRG, CRT, 0, s>>>(ncoarse(M), f, M->w.partial);
-    k_cfinish<NV><<<1, 32, 0, s>>>(M->w.partial, M->w.scal);
+    k_cfinish<NV><<<1, 32, 0, s>>>(M->w.partial, M->w.scal + slot);
     MGC_CUDA(cudaGetLastError());
     count(2, (double)ncoarse(M) * 8.0 * 2);
     return MGC_OK;
@@ -617,25 +636,30 @@ int build(mgc_mg_s *M, cudaStream_t s)
     return MGC_OK;
 }
 
-// BiCGStab on D_c x = b (coarse FP32 vectors) to tol or maxit
+// BiCGStab on D_c x = b (coarse FP32 vectors) to tol or maxit.  The scalars
+// stay on the device (the update kernels form alpha, omega and beta from
+// them); the host reads ||r||^2 once per iteration to stop.
 int coarse_solve(mgc_mg_s *M, const float2 *b, float2 *x, double tol, int maxit, int *iters, cudaStream_t s)
 {
     MgWork &w = M->w;
     const int n = ncoarse(M);
     float2 *r = w.cr, *r0 = w.cr0, *p = w.cp, *v = w.cv, *sv = w.cs, *t = w.ct;
+    const double *sc = w.scal;
     MGC_CUDA(cudaMemcpyAsync(r, b, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     MGC_CUDA(cudaMemcpyAsync(r0, b, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     MGC_CUDA(cudaMemcpyAsync(p, b, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(float2), s));
-    double h[3];
+    // ||b||^2 into CS_RR, rho = <r0, r> into CS_RHO (two slots after it)
     MGC_TRY(creduce<3>(M, [=] __device__(int e, double *acc) {
         const float2 q = r[e];
         acc[0] += (double)q.x * q.x + (double)q.y * q.y;
         ddot(acc + 1, r0[e], q);
-    }, s));
-    MGC_TRY(read_scalars(M, 3, h, s));
-    const double bn = std::sqrt(h[0]);
-    zd rho(h[1], h[2]);
+    }, s, CS_RR));
+    MGC_CUDA(cudaMemcpyAsync(w.scal + CS_RHO, w.scal + CS_RHO1, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double h;
+    MGC_CUDA(cudaMemcpyAsync(w.hscal, w.scal + CS_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MGC_CUDA(cudaStreamSynchronize(s));
+    const double bn = std::sqrt(w.hscal[0]);
     int it = 0;
     if (bn == 0.0) {
         *iters = 0;
@@ -643,42 +667,40 @@ int coarse_solve(mgc_mg_s *M, const float2 *b, float2 *x, double tol, int maxit,
     }
     while (it < maxit) {
         MGC_TRY(coarse_apply(M, p, v, s));
-        MGC_TRY(creduce<2>(M, [=] __device__(int e, double *acc) { ddot(acc, r0[e], v[e]); }, s));
-        MGC_TRY(read_scalars(M, 2, h, s));
-        const zd r0v(h[0], h[1]);
-        if (r0v == zd(0, 0) || !std::isfinite(h[0]) || !std::isfinite(h[1])) break;
-        const zd alpha = rho / r0v;
-        const float2 a = make_float2((float)alpha.real(), (float)alpha.imag());
-        MGC_TRY(cmap(M, [=] __device__(int e) { sv[e] = cmad(make_float2(-a.x, -a.y), v[e], r[e]); }, s));
+        MGC_TRY(creduce<2>(M, [=] __device__(int e, double *acc) { ddot(acc, r0[e], v[e]); }, s, CS_R0V));
+        MGC_TRY(cmap(M, [=] __device__(int e) {
+            const float2 a = tof(cs_alpha(sc));
+            sv[e] = cmad(make_float2(-a.x, -a.y), v[e], r[e]);
+        }, s));
         MGC_TRY(coarse_apply(M, sv, t, s));
         MGC_TRY(creduce<3>(M, [=] __device__(int e, double *acc) {
             const float2 q = t[e];
             acc[0] += (double)q.x * q.x + (double)q.y * q.y;
             ddot(acc + 1, q, sv[e]);
-        }, s));
-        MGC_TRY(read_scalars(M, 3, h, s));
-        const zd omega = h[0] > 0 ? zd(h[1], h[2]) / h[0] : zd(0, 0);
-        const float2 o = make_float2((float)omega.real(), (float)omega.imag());
+        }, s, CS_TT));
         MGC_TRY(creduce<3>(M, [=] __device__(int e, double *acc) {
+            const float2 a = tof(cs_alpha(sc)), o = tof(cs_omega(sc));
             x[e] = cmad(o, sv[e], cmad(a, p[e], x[e]));
             const float2 q = cmad(make_float2(-o.x, -o.y), t[e], sv[e]);
             r[e] = q;
             acc[0] += (double)q.x * q.x + (double)q.y * q.y;
             ddot(acc + 1, r0[e], q);
-        }, s));
-        MGC_TRY(read_scalars(M, 3, h, s));
+        }, s, CS_RR));
+        MGC_CUDA(cudaMemcpyAsync(w.hscal, w.scal + CS_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MGC_CUDA(cudaStreamSynchronize(s));
+        h = w.hscal[0];
         ++it;
-        if (!std::isfinite(h[0])) return fail(MGC_ERR_BREAKDOWN, "coarse BiCGStab: non-finite residual");
-        if (std::sqrt(h[0]) <= tol * bn) break;
-        const zd rho1(h[1], h[2]);
-        if (rho == zd(0, 0) || omega == zd(0, 0)) break;
-        const zd beta = (rho1 / rho) * (alpha / omega);
-        const float2 bt = make_float2((float)beta.real(), (float)beta.imag());
+        if (!std::isfinite(h)) return fail(MGC_ERR_BREAKDOWN, "coarse BiCGStab: non-finite residual");
+        if (std::sqrt(h) <= tol * bn) break;
+        // p = r + beta (p - omega v), beta = (rho1 / rho)(alpha / omega); then rho = rho1
         MGC_TRY(cmap(M, [=] __device__(int e) {
+            const double2 om = cs_omega(sc);
+            const double2 beta = zmul(zdiv(ldz(sc + CS_RHO1), ldz(sc + CS_RHO)), zdiv(cs_alpha(sc), om));
+            const float2 o = tof(om), bt = tof(beta);
             const float2 q = cmad(make_float2(-o.x, -o.y), v[e], p[e]);
             p[e] = cmad(bt, q, r[e]);
         }, s));
-        rho = rho1;
+        MGC_CUDA(cudaMemcpyAsync(w.scal + CS_RHO, w.scal + CS_RHO1, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     *iters = it;
     return MGC_OK;
@@ -806,8 +828,8 @@ int mgc_mg_create(mgc_clover_t op, const int agg[4], int nvec, mgc_mg_t *out)
         okm = okm && cudaMalloc(&w.l16a, spinor_bytes(g, 16, 1)) == cudaSuccess &&
               cudaMalloc(&w.l16b, spinor_bytes(g, 16, 1)) == cudaSuccess;
     okm = okm && cudaMalloc(&w.partial, CRG * 4 * sizeof(double)) == cudaSuccess &&
-          cudaMalloc(&w.scal, 8 * sizeof(double)) == cudaSuccess && cudaMalloc(&w.dbad, sizeof(int)) == cudaSuccess &&
-          cudaMallocHost(&w.hscal, 8 * sizeof(double)) == cudaSuccess;
+          cudaMalloc(&w.scal, 16 * sizeof(double)) == cudaSuccess && cudaMalloc(&w.dbad, sizeof(int)) == cudaSuccess &&
+          cudaMallocHost(&w.hscal, 16 * sizeof(double)) == cudaSuccess;
     if (!okm) {
         cudaGetLastError();
         mg_free(M);
@@ -888,6 +910,7 @@ int mgc_mg_setup(mgc_mg_t M, const double *eta, const mgc_mg_params *p, void *st
             MGC_CUDA(cudaMemcpyAsync(vi, w.f4, fine32_bytes(M), cudaMemcpyDeviceToDevice, s));
             k_fscale<<<fgrid(fine4(M), 256), 256, 0, s>>>(fine4(M), (float)(1.0 / std::sqrt(n2)), vi);
             MGC_CUDA(cudaGetLastError());
+            count(1, 2.0 * fine32_bytes(M));
         }
         MGC_TRY(build(M, s));
     }

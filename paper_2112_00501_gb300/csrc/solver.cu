@@ -53,6 +53,9 @@ enum {
     S_R0V = 7,     // <r0, v> (2)
     S_TS = 9,      // <t, s> (2)
     S_TT = 11,     // <t, t>
+    S_ALPHA = 14,  // BiCGStab alpha, omega, beta, formed once per iteration (2 slots each)
+    S_OMEGA = 16,
+    S_BETAB = 18,
     S_BETA = 32,   // CGS coefficients, 2 * MAXM slots
     S_TOTAL = 32 + 2 * MAXM,
 };
@@ -137,6 +140,20 @@ __global__ void __launch_bounds__(RT) k_reduce(long long n, F f, double *partial
         for (int k = 0; k < NV; ++k) out[k] = acc[k];
         *counter = 0;
     }
+}
+
+// one thread forming scalars from scalars (no per-element FP64 divisions)
+template <class F>
+__global__ void k_scalar(F f)
+{
+    f();
+}
+
+template <class F>
+static void scalar_step(F f, cudaStream_t s)
+{
+    k_scalar<<<1, 1, 0, s>>>(f);
+    count(1, 0);
 }
 
 // a plain elementwise map
@@ -383,12 +400,19 @@ static int fgcr(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *inf
                     acc_dot(acc + 1, wv, r[e]);
                 },
                 W, sc + S_NW, s, 2 * j + 5));
-            // normalise, then x += alpha z_j, r -= alpha w_j; ||r||^2
+            // normalise, then x += alpha z_j, r -= alpha w_j; ||r||^2 (1/||w_j|| and
+            // alpha formed once, not per element)
+            scalar_step([=] __device__() {
+                const double inv = 1.0 / sqrt(sc[S_NW]);
+                sc[S_ALPHA] = sc[S_WR] * inv;
+                sc[S_ALPHA + 1] = sc[S_WR + 1] * inv;
+                sc[S_OMEGA] = inv;
+            }, s);
             MGC_TRY(reduce<1>(
                 n,
                 [=] __device__(long long e, double *acc) {
-                    const double inv = 1.0 / sqrt(sc[S_NW]);
-                    const double2 alpha = make_double2(sc[S_WR] * inv, sc[S_WR + 1] * inv);
+                    const double inv = sc[S_OMEGA];
+                    const double2 alpha = ld2(sc + S_ALPHA);
                     double2 wv = wj[e], zv = zj[e];
                     wv = make_double2(wv.x * inv, wv.y * inv);
                     zv = make_double2(zv.x * inv, zv.y * inv);
@@ -485,13 +509,15 @@ static int fbicgstab_impl(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve
             MGC_TRY(pre(pv, ph));
             MGC_TRY(apply_D64(op, ph, v, s));
             MGC_TRY(reduce<2>(n, [=] __device__(long long e, double *acc) { acc_dot(acc, r0[e], v[e]); }, W, sc + S_R0V, s, 2));
+            scalar_step([=] __device__() {
+                const double2 a = cdiv(ld2(sc + S_RHO), ld2(sc + S_R0V));
+                sc[S_ALPHA] = a.x;
+                sc[S_ALPHA + 1] = a.y;
+            }, s);
             // s = r - alpha v
             MGC_TRY(map(
                 n,
-                [=] __device__(long long e) {
-                    const double2 alpha = cdiv(ld2(sc + S_RHO), ld2(sc + S_R0V));
-                    sv[e] = csub(r[e], cmul(alpha, v[e]));
-                },
+                [=] __device__(long long e) { sv[e] = csub(r[e], cmul(ld2(sc + S_ALPHA), v[e])); },
                 s, 3));
             MGC_TRY(pre(sv, sh));
             MGC_TRY(apply_D64(op, sh, t, s));
@@ -502,13 +528,16 @@ static int fbicgstab_impl(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve
                     acc_n2(acc + 2, t[e]);
                 },
                 W, sc + S_TS, s, 2));
+            scalar_step([=] __device__() {
+                const double tt = sc[S_TT];
+                sc[S_OMEGA] = tt > 0 ? sc[S_TS] / tt : 0.0;
+                sc[S_OMEGA + 1] = tt > 0 ? sc[S_TS + 1] / tt : 0.0;
+            }, s);
             // x += alpha ph + omega sh, r = s - omega t; ||r||^2 and <r0, r>
             MGC_TRY(reduce<3>(
                 n,
                 [=] __device__(long long e, double *acc) {
-                    const double2 alpha = cdiv(ld2(sc + S_RHO), ld2(sc + S_R0V));
-                    const double tt = sc[S_TT];
-                    const double2 omega = tt > 0 ? make_double2(sc[S_TS] / tt, sc[S_TS + 1] / tt) : make_double2(0, 0);
+                    const double2 alpha = ld2(sc + S_ALPHA), omega = ld2(sc + S_OMEGA);
                     x[e] = cadd(x[e], cadd(cmul(alpha, ph[e]), cmul(omega, sh[e])));
                     const double2 rv = csub(sv[e], cmul(omega, t[e]));
                     r[e] = rv;
@@ -531,15 +560,16 @@ static int fbicgstab_impl(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve
             if (rr <= tol2) break;
             if (h[1] == 0.0 && h[2] == 0.0) { restart = true; break; }
             // p = r + beta (p - omega v), beta = (rho1 / rho)(alpha / omega); rho = rho1
+            scalar_step([=] __device__() {
+                const double2 beta = cmul(cdiv(ld2(sc + S_RR + 1), ld2(sc + S_RHO)),
+                                          cdiv(ld2(sc + S_ALPHA), ld2(sc + S_OMEGA)));
+                sc[S_BETAB] = beta.x;
+                sc[S_BETAB + 1] = beta.y;
+            }, s);
             MGC_TRY(map(
                 n,
                 [=] __device__(long long e) {
-                    const double2 rho = ld2(sc + S_RHO);
-                    const double2 rho1 = ld2(sc + S_RR + 1);
-                    const double2 alpha = cdiv(rho, ld2(sc + S_R0V));
-                    const double tt = sc[S_TT];
-                    const double2 omega = make_double2(sc[S_TS] / tt, sc[S_TS + 1] / tt);
-                    const double2 beta = cmul(cdiv(rho1, rho), cdiv(alpha, omega));
+                    const double2 beta = ld2(sc + S_BETAB), omega = ld2(sc + S_OMEGA);
                     pv[e] = cadd(r[e], cmul(beta, csub(pv[e], cmul(omega, v[e]))));
                 },
                 s, 4));
