@@ -564,6 +564,102 @@ void or_mr_block_at(const int *L, const int *Bd, const int *bc, double kappa, do
     free(Cb);
 }
 
+/* kappa H_B v on one block (Dirichlet), as v - D_B v with the clover set to 1 */
+static void hop_block(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U, const cplx *v,
+                      cplx *out)
+{
+    long VB = block_volume(Bd), n = VB * 12;
+    cplx *one = calloc(VB * 144, sizeof(cplx));
+    cplx *t = malloc(sizeof(cplx) * n);
+    for (long l = 0; l < VB; ++l)
+        for (int i = 0; i < 12; ++i) one[l * 144 + i * 12 + i] = 1;
+    dirac_block_impl(L, Bd, bc, kappa, U, one, 1, v, t, 0);
+    for (long i = 0; i < n; ++i) out[i] = v[i] - t[i];
+    free(one);
+    free(t);
+}
+
+/* parity of the local (lexicographic) block site l; blocks start at even
+ * coordinates, so it is the site's global parity */
+static int block_parity(const int *Bd, long l)
+{
+    int s = 0;
+    for (int mu = 0; mu < 4; ++mu) {
+        s += (int)(l % Bd[mu]);
+        l /= Bd[mu];
+    }
+    return s & 1;
+}
+
+/* out = M in site by site over the block (M = C or C^-1 of the block's sites),
+ * only on sites of the given parity (others set to 0) */
+static void block_site_mul(const int *L, const int *Bd, const int *bc, const cplx *M, int parity, const cplx *in,
+                           cplx *out)
+{
+    long VB = block_volume(Bd);
+    for (long l = 0; l < VB; ++l) {
+        const cplx *m = M + block_site(L, Bd, bc, l) * 144;
+        for (int i = 0; i < 12; ++i) {
+            cplx a = 0;
+            if (block_parity(Bd, l) == parity)
+                for (int j = 0; j < 12; ++j) a += m[i * 12 + j] * in[l * 12 + j];
+            out[l * 12 + i] = a;
+        }
+    }
+}
+
+/*
+ * Even-odd preconditioned minimal residual on D_B (the block solver of
+ * DD-alphaAMG): with the block's sites split by parity,
+ * D_B = [[C_ee, -kappa H_eo], [-kappa H_oe, C_oo]]; nmr MR steps from 0 on the
+ * even Schur complement  Dh = C_ee - kappa^2 H_eo C_oo^-1 H_oe  with source
+ * rh = r_e + kappa H_eo C_oo^-1 r_o, then e_o = C_oo^-1 (r_o + kappa H_oe e_e).
+ */
+static void mr_eo_block_impl(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U, const cplx *C,
+                             const cplx *Ci, const cplx *r_b, cplx *e_b, int nmr)
+{
+    long VB = block_volume(Bd), n = VB * 12;
+    cplx *t = malloc(sizeof(cplx) * n), *h = malloc(sizeof(cplx) * n), *rho = malloc(sizeof(cplx) * n);
+    cplx *p = malloc(sizeof(cplx) * n), *y = malloc(sizeof(cplx) * n), *ee = calloc(n, sizeof(cplx));
+    /* rh = r_e + kappa H_eo C_oo^-1 r_o (even sites) */
+    block_site_mul(L, Bd, bc, Ci, 1, r_b, t);
+    hop_block(L, Bd, bc, kappa, U, t, h);
+    for (long l = 0; l < VB; ++l)
+        for (int i = 0; i < 12; ++i)
+            rho[l * 12 + i] = block_parity(Bd, l) == 0 ? r_b[l * 12 + i] + h[l * 12 + i] : 0;
+    for (int k = 0; k < nmr; ++k) {
+        /* p = Dh rho = C_ee rho - kappa H_eo C_oo^-1 (kappa H_oe rho) */
+        hop_block(L, Bd, bc, kappa, U, rho, h);
+        block_site_mul(L, Bd, bc, Ci, 1, h, y);
+        hop_block(L, Bd, bc, kappa, U, y, h);
+        block_site_mul(L, Bd, bc, C, 0, rho, p);
+        for (long l = 0; l < VB; ++l)
+            if (block_parity(Bd, l) == 0)
+                for (int i = 0; i < 12; ++i) p[l * 12 + i] -= h[l * 12 + i];
+        cplx pr = vdot(n, p, rho);
+        double pp = vnorm2(n, p);
+        cplx alpha = (pp > 0) ? pr / pp : 0;
+        for (long i = 0; i < n; ++i) {
+            ee[i] += alpha * rho[i];
+            rho[i] -= alpha * p[i];
+        }
+    }
+    /* e_o = C_oo^-1 (r_o + kappa H_oe e_e) */
+    hop_block(L, Bd, bc, kappa, U, ee, h);
+    for (long l = 0; l < VB; ++l)
+        for (int i = 0; i < 12; ++i) t[l * 12 + i] = block_parity(Bd, l) == 1 ? r_b[l * 12 + i] + h[l * 12 + i] : 0;
+    block_site_mul(L, Bd, bc, Ci, 1, t, y);
+    for (long l = 0; l < VB; ++l)
+        for (int i = 0; i < 12; ++i) e_b[l * 12 + i] = block_parity(Bd, l) == 0 ? ee[l * 12 + i] : y[l * 12 + i];
+    free(t); free(h); free(rho); free(p); free(y); free(ee);
+}
+
+void or_mr_eo_block(const int *L, const int *Bd, const int *bc, double kappa, const cplx *U, const cplx *C,
+                    const cplx *Ci, const cplx *r_b, cplx *e_b, int nmr)
+{
+    mr_eo_block_impl(L, Bd, bc, kappa, U, C, Ci, r_b, e_b, nmr);
+}
+
 /*
  * n_cy multiplicative SAP sweeps on D x = b, x updated in place.  Each sweep
  * visits colour 0 then colour 1; within a colour every block B gets
@@ -571,8 +667,8 @@ void or_mr_block_at(const int *L, const int *Bd, const int *bc, double kappa, do
  * other, so the residual of a colour is taken once before its blocks are
  * visited.  Requires L[mu] / Bd[mu] even for every mu.
  */
-void or_sap(const int *L, const int *Bd, int tbc, double kappa, const cplx *U, const cplx *C,
-            const cplx *b, cplx *x, int ncy, int nmr)
+static void sap_impl(const int *L, const int *Bd, int tbc, double kappa, const cplx *U, const cplx *C,
+                     const cplx *Ci, const cplx *b, cplx *x, int ncy, int nmr, int eo)
 {
     long V = vol4(L);
     long VB = block_volume(Bd);
@@ -596,7 +692,8 @@ void or_sap(const int *L, const int *Bd, int tbc, double kappa, const cplx *U, c
                     long s = block_site(L, Bd, bc, l);
                     for (int i = 0; i < 12; ++i) rb[l * 12 + i] = r[s * 12 + i];
                 }
-                or_mr_block(L, Bd, bc, kappa, U, C, rb, eb, NULL, nmr);
+                if (eo) mr_eo_block_impl(L, Bd, bc, kappa, U, C, Ci, rb, eb, nmr);
+                else or_mr_block(L, Bd, bc, kappa, U, C, rb, eb, NULL, nmr);
                 for (long l = 0; l < VB; ++l) {
                     long s = block_site(L, Bd, bc, l);
                     for (int i = 0; i < 12; ++i) x[s * 12 + i] += eb[l * 12 + i];
@@ -823,6 +920,19 @@ done:
     free(r); free(ra); free(rhs); free(y); free(rr); free(r0); free(p); free(v); free(s); free(t); free(tmp);
     free(e);
     return status;
+}
+
+void or_sap(const int *L, const int *Bd, int tbc, double kappa, const cplx *U, const cplx *C,
+            const cplx *b, cplx *x, int ncy, int nmr)
+{
+    sap_impl(L, Bd, tbc, kappa, U, C, NULL, b, x, ncy, nmr, 0);
+}
+
+/* the same sweeps with the even-odd preconditioned MR block solver */
+void or_sap_eo(const int *L, const int *Bd, int tbc, double kappa, const cplx *U, const cplx *C, const cplx *Ci,
+               const cplx *b, cplx *x, int ncy, int nmr)
+{
+    sap_impl(L, Bd, tbc, kappa, U, C, Ci, b, x, ncy, nmr, 1);
 }
 
 /* ------------------------------------------------------------------ */

@@ -54,6 +54,8 @@ def lib():
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.or_solve.restype = C.c_int
         L.or_force.argtypes = [_i4, C.c_int, C.c_double, C.c_double, _c16, _c16, _c16, _c16]
+        L.or_mr_eo_block.argtypes = [_i4, _i4, _i4, C.c_double, _c16, _c16, _c16, _c16, _c16, C.c_int]
+        L.or_sap_eo.argtypes = [_i4, _i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, _c16, C.c_int, C.c_int]
         L.or_apply_A.argtypes = [_i4, C.c_int, C.c_double, _c16, _c16, _c16, _c16, _c16]
         L.or_jacobi_block.argtypes = [_i4, _i4, _i4, C.c_double, _c16, _c16, _c16, _c16, _c16, C.c_int]
         L.or_jacobi_block_at.argtypes = [_i4, _i4, _i4, C.c_double, C.c_double, _c16, _c16, _c16, C.c_int]
@@ -248,6 +250,26 @@ def sap(dims, bdims, tbc, kappa, U, Cl, b, x0=None, ncy=4, nmr=4):
     lib().or_sap(_dims(dims), _dims(bdims), int(tbc), float(kappa), _sized(U, V * 36, "U"), _sized(Cl, V * 144, "Cl"),
                  b, x,
                  int(ncy), int(nmr))
+    return x
+
+
+def mr_eo_block(dims, bdims, bc, kappa, U, Cl, Ci, r, nmr):
+    """Even-odd preconditioned MR on one domain (Schur complement on even sites)."""
+    V = _vol(dims)
+    r = _sized(r, _vb(bdims) * 12, "r")
+    e = np.zeros_like(r)
+    lib().or_mr_eo_block(_dims(dims), _dims(bdims), _dims(bc), float(kappa), _sized(U, V * 36, "U"),
+                         _sized(Cl, V * 144, "Cl"), _sized(Ci, V * 144, "Ci"), r, e, int(nmr))
+    return e
+
+
+def sap_eo(dims, bdims, tbc, kappa, U, Cl, Ci, b, x0=None, ncy=4, nmr=4):
+    """n_cy SAP sweeps on D x = b with even-odd preconditioned MR domain solves."""
+    V = _vol(dims)
+    b = _sized(b, V * 12, "b")
+    x = np.zeros_like(b) if x0 is None else _sized(np.array(x0, dtype=np.complex128, copy=True), V * 12, "x0")
+    lib().or_sap_eo(_dims(dims), _dims(bdims), int(tbc), float(kappa), _sized(U, V * 36, "U"),
+                    _sized(Cl, V * 144, "Cl"), _sized(Ci, V * 144, "Ci"), b, x, int(ncy), int(nmr))
     return x
 
 
