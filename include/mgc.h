@@ -186,6 +186,16 @@ int mgc_sap_smooth(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, 
                    int prec, int x_is_zero, void *stream);
 
 /*
+ * mgc_sap_smooth with the even-odd preconditioned MR domain solver of
+ * DD-alphaAMG (which the paper's multigrid follows, Sec. 3): on each domain,
+ * n_mr MR steps on the even-site Schur complement
+ * C_ee - kappa^2 H_eo C_oo^-1 H_oe with source r_e + kappa H_eo C_oo^-1 r_o, then
+ * e_o = C_oo^-1 (r_o + kappa H_oe e_e).  Same arguments as mgc_sap_smooth.
+ */
+int mgc_sap_smooth_eo(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, int n_mr, int prec,
+                      int x_is_zero, void *stream);
+
+/*
  * QWS's clover-preconditioned operator (Sec. 2): out = A in with
  * A = C^-1 D = 1 - kappa C^-1 H, for nrhs packed spinors at precision prec
  * (64, or 32/16 when the gauge keeps that copy).  Asynchronous.
@@ -228,6 +238,7 @@ typedef struct {
     int on_device;     /* 1: b, x are device pointers; 0: host pointers */
     int x_is_guess;    /* 1: x holds the initial guess; 0: start from x = 0 */
     double inner_tol;  /* method 2: relative residual reduction of each inner solve */
+    int sap_solver;    /* SAP domain solver of methods 0-2: 0 = MR, 2 = even-odd preconditioned MR */
 } mgc_solve_params;
 
 typedef struct {

@@ -35,6 +35,7 @@ class SolveParams(C.Structure):
         ("on_device", C.c_int),
         ("x_is_guess", C.c_int),
         ("inner_tol", C.c_double),
+        ("sap_solver", C.c_int),
     ]
 
 
@@ -86,6 +87,7 @@ SIGNATURES = {
     "mgc_apply_clover": (_I, [_P, _P, _P, _I, _I, _I, _P]),
     "mgc_sap_smooth": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P]),
     "mgc_apply_A": (_I, [_P, _P, _P, _I, _I, _P]),
+    "mgc_sap_smooth_eo": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P]),
     "mgc_sap_smooth_A": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P]),
     "mgc_solve_params_default": (None, [C.POINTER(SolveParams)]),
     "mgc_solve": (_I, [_P, _P, _P, _I, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P]),

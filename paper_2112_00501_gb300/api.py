@@ -172,6 +172,22 @@ class CloverOperator:
                                       _stream(stream)), "mgc_sap_smooth")
         return x
 
+    def sap_smooth_eo(self, b: torch.Tensor, x: torch.Tensor, prec: int, nrhs: int = 1, n_cy: int = 4,
+                      n_mr: int = 4, x_is_zero: bool = False, stream=None) -> torch.Tensor:
+        """SAP sweeps with even-odd preconditioned MR domain solves, packed fields."""
+        check(self.lib.mgc_sap_smooth_eo(self.handle, _ptr(b), _ptr(x), nrhs, n_cy, n_mr, prec,
+                                         int(bool(x_is_zero)), _stream(stream)), "mgc_sap_smooth_eo")
+        return x
+
+    def sap_eo(self, b, prec: int = 64, n_cy: int = 4, n_mr: int = 4, x0=None) -> torch.Tensor:
+        """n_cy SAP sweeps with even-odd MR domain solves on D x = b, canonical in and out."""
+        b = _canon(b, "cuda")
+        nrhs = 1 if b.dim() == 3 else b.shape[0]
+        bp = self.lattice.pack(b, prec)
+        xp = self.lattice.zeros_packed(prec, nrhs) if x0 is None else self.lattice.pack(_canon(x0, "cuda"), prec)
+        self.sap_smooth_eo(bp, xp, prec, nrhs, n_cy, n_mr, x_is_zero=x0 is None)
+        return self.lattice.unpack(xp, prec, nrhs)
+
     def apply_A(self, x: torch.Tensor, prec: int, nrhs: int = 1, out=None, stream=None) -> torch.Tensor:
         """A x with A = C^-1 D (QWS's operator), packed fields."""
         if out is None:

@@ -388,6 +388,14 @@ int mgc_sap_smooth(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, 
     return launch_sap(op, prec, b, x, nrhs, n_cy, n_mr, x_is_zero, (cudaStream_t)stream);
 }
 
+int mgc_sap_smooth_eo(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, int n_mr, int prec,
+                      int x_is_zero, void *stream)
+{
+    MGC_TRY(check_apply(op, b, x, nrhs, prec));
+    if (n_cy < 0 || n_mr < 0) return fail(MGC_ERR_INVALID_ARG, "n_cy and n_mr must be >= 0");
+    return launch_sap_eo(op, prec, b, x, nrhs, n_cy, n_mr, x_is_zero, (cudaStream_t)stream);
+}
+
 int mgc_apply_A(mgc_clover_t op, const void *in, void *out, int nrhs, int prec, void *stream)
 {
     MGC_TRY(check_apply(op, in, out, nrhs, prec));
@@ -416,6 +424,7 @@ void mgc_solve_params_default(mgc_solve_params *p)
     p->on_device = 1;
     p->x_is_guess = 0;
     p->inner_tol = 2e-6;
+    p->sap_solver = 0;
 }
 
 int mgc_solve(mgc_clover_t op, const double *b, double *x, int nrhs, const mgc_solve_params *p, mgc_solve_info *info,

@@ -1044,6 +1044,7 @@ int mgc_batch_solve(mgc_batch_t B, const double *const *rhs, double *const *x, c
         return fail(MGC_ERR_INVALID_ARG, "the batched solve is the two-level method with SAP (method 2, precond 1)");
     if (p->smoother_prec != 32 && p->smoother_prec != 16)
         return fail(MGC_ERR_INVALID_ARG, "smoother_prec must be 32 or 16");
+    if (p->sap_solver != 0) return fail(MGC_ERR_INVALID_ARG, "the batched solve uses the MR domain solver (sap_solver 0)");
     if (!has_prec(B->spec.ops[0]->gauge, p->smoother_prec) || !has_prec(B->spec.ops[0]->gauge, 32))
         return fail(MGC_ERR_INVALID_ARG, "the operators keep no copy at the smoother precision");
     if (p->restart < 1 || p->n_cy < 1 || p->n_mr < 1 || !(p->tol > 0) || p->max_iter < 1 || !(p->inner_tol > 0))

@@ -12,17 +12,29 @@
 // Domains of one colour never touch each other, so the launches of a sweep
 // are red then black and every block of a launch is independent.
 //
-// With JAC = true the same kernels run QWS's smoother for the clover-
+// In mode SAP_JAC the same kernels run QWS's smoother for the clover-
 // preconditioned operator A = C^-1 D = 1 - kappa C^-1 H (Sec. 2): the staged
 // clover term is C^-1, the domain residual is r_B = (b - x + kappa C^-1 H x)|_B,
 // and the domain solve is a fixed number n_j of Jacobi iterations
 // e <- r_B + kappa C^-1 H_B e from e = 0 (the first gives e = r_B), with e
 // (instead of r) in shared memory and no block reductions.
+//
+// In mode SAP_EO (FP64 and staged kernels) the domain solve is the even-odd
+// preconditioned MR of DD-alphaAMG: the even sites (the first half of a domain
+// in the packed order) run MR on the Schur complement
+// C_ee - kappa^2 H_eo C_oo^-1 H_oe with source r_e + kappa H_eo C_oo^-1 r_o,
+// the odd sites apply C_oo^-1 (read from global memory) in between and finally
+// form e_o = C_oo^-1 (r_o + kappa H_oe e_e).  Odd entries of the shared vector
+// hold the odd-site intermediate, even entries the even-site residual.
 #include "hop.cuh"
 #include "mgc_host.h"
 #include "tma.cuh"
 
 namespace mgc {
+
+// domain solvers of the smoother kernels: MR on D_B; Jacobi on A_B (QWS);
+// even-odd preconditioned MR on D_B (MR on the even Schur complement)
+enum { SAP_MR = 0, SAP_JAC = 1, SAP_EO = 2 };
 
 // sum of three values over the thread block, identical on every thread
 template <typename T>
@@ -81,8 +93,8 @@ __device__ __forceinline__ void block_hop_dir(const GA &U, int blkbase, int i, i
     }
 }
 
-template <bool JAC, class SP, class GA, class CL>
-__global__ void __launch_bounds__(256) k_sap_colour(Geom g, SP b, SP x, GA U, CL C, typename SP::Real kappa,
+template <int MODE, class SP, class GA, class CL>
+__global__ void __launch_bounds__(256) k_sap_colour(Geom g, SP b, SP x, GA U, CL C, CL Ci, typename SP::Real kappa,
                                                     int colour, int nmr, int x_zero)
 {
     using T = typename SP::Real;
@@ -118,7 +130,7 @@ __global__ void __launch_bounds__(256) k_sap_colour(Geom g, SP b, SP x, GA U, CL
     Cx<T> rv[12];
     bb.load(i, rv);
     if (!x_zero) {
-        if (JAC) {
+        if (MODE == SAP_JAC) {
             Cx<T> acc[12], t[12], xo[12];
             hop_site<false>(g, c, i, xx, U, acc);
             clover_site(C, i, acc, t);
@@ -150,8 +162,89 @@ __global__ void __launch_bounds__(256) k_sap_colour(Geom g, SP b, SP x, GA U, CL
     for (int k = 0; k < 12; ++k) e[k] = Cx<T>{0, 0};
     __syncthreads();
 
+    // 2''. even-odd preconditioned MR
+    if (MODE == SAP_EO) {
+        const bool even = l < (vb >> 1);
+        Cx<T> rho[12], t[12], acc[12];
+        auto hops = [&]() {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k] = Cx<T>{0, 0};
+            block_hop_dir<0>(U, blkbase, i, nf[0], nb[0], rs, vb, acc);
+            block_hop_dir<1>(U, blkbase, i, nf[1], nb[1], rs, vb, acc);
+            block_hop_dir<2>(U, blkbase, i, nf[2], nb[2], rs, vb, acc);
+            block_hop_dir<3>(U, blkbase, i, nf[3], nb[3], rs, vb, acc);
+        };
+        // rho = r_e + kappa H_eo C_oo^-1 r_o
+        if (!even) {
+            clover_site(Ci, i, rv, t);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rs[k * vb + l] = t[k];
+        }
+        __syncthreads();
+        if (even) {
+            hops();
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                rho[k] = Cx<T>{fma(kappa, acc[k].r, rv[k].r), fma(kappa, acc[k].i, rv[k].i)};
+        }
+        __syncthreads();
+        if (even)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rs[k * vb + l] = rho[k];
+        __syncthreads();
+        for (int it = 0; it < nmr; ++it) {
+            // odd sites: y = C_oo^-1 (kappa H_oe rho)
+            if (!even) {
+                hops();
+#pragma unroll
+                for (int k = 0; k < 12; ++k) acc[k] = kappa * acc[k];
+                clover_site(Ci, i, acc, t);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) rs[k * vb + l] = t[k];
+            }
+            __syncthreads();
+            // even sites: p = C_ee rho - kappa H_eo y, MR step
+            T pr = 0, pi = 0, pp = 0;
+            Cx<T> p[12];
+            if (even) {
+                hops();
+                clover_site(C, i, rho, p);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    p[k] = Cx<T>{fma(-kappa, acc[k].r, p[k].r), fma(-kappa, acc[k].i, p[k].i)};
+                    pr = fma(p[k].r, rho[k].r, fma(p[k].i, rho[k].i, pr));
+                    pi = fma(p[k].r, rho[k].i, fma(-p[k].i, rho[k].r, pi));
+                    pp = fma(p[k].r, p[k].r, fma(p[k].i, p[k].i, pp));
+                }
+            }
+            block_sum3(pr, pi, pp, red);
+            const Cx<T> alpha = (pp > 0) ? Cx<T>{pr / pp, pi / pp} : Cx<T>{0, 0};
+            if (even)
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    e[k] = cfma(alpha, rho[k], e[k]);
+                    rho[k] = rho[k] - alpha * p[k];
+                    rs[k * vb + l] = rho[k];
+                }
+            __syncthreads();
+        }
+        // e_o = C_oo^-1 (r_o + kappa H_oe e_e)
+        if (even)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rs[k * vb + l] = e[k];
+        __syncthreads();
+        if (!even) {
+            hops();
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                t[k] = Cx<T>{fma(kappa, acc[k].r, rv[k].r), fma(kappa, acc[k].i, rv[k].i)};
+            clover_site(Ci, i, t, e);
+        }
+        nmr = 0;
+    }
+
     // 2'. Jacobi on A_B: e_1 = r_B, then e <- r_B + kappa C^-1 H_B e
-    if (JAC) {
+    if (MODE == SAP_JAC) {
         if (nmr >= 1)
 #pragma unroll
             for (int k = 0; k < 12; ++k) e[k] = rv[k];
@@ -420,22 +513,23 @@ static size_t staged_smem(int vb)
 }
 
 // one domain solve of the staged kernel: domain jb of `colour`, right-hand side rr
-template <bool JAC, class SP, class GA, class CL>
+template <int MODE, class SP, class GA, class CL>
 __device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, const SP &x, const GA &U, const CL &C,
-                                                float kappa, int colour, int nmr, int x_zero, int *status, int jb,
-                                                int rr);
+                                                const CL &Ci, float kappa, int colour, int nmr, int x_zero,
+                                                int *status, int jb, int rr);
 
-template <bool JAC, class SP, class GA, class CL>
-__global__ void __launch_bounds__(256, staged_min_ctas<GA, CL>())
-    k_sap_staged(Geom g, SP b, SP x, GA U, CL C, float kappa, int colour, int nmr, int x_zero, int *status)
+// the even-odd solver keeps more state per thread: one block per SM
+template <int MODE, class SP, class GA, class CL>
+__global__ void __launch_bounds__(256, MODE == SAP_EO ? 1 : staged_min_ctas<GA, CL>())
+    k_sap_staged(Geom g, SP b, SP x, GA U, CL C, CL Ci, float kappa, int colour, int nmr, int x_zero, int *status)
 {
-    sap_staged_body<JAC>(g, b, x, U, C, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
+    sap_staged_body<MODE>(g, b, x, U, C, Ci, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
 }
 
-template <bool JAC, class SP, class GA, class CL>
+template <int MODE, class SP, class GA, class CL>
 __device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, const SP &x, const GA &U, const CL &C,
-                                                float kappa, int colour, int nmr, int x_zero, int *status, int jb,
-                                                int rr)
+                                                const CL &Ci, float kappa, int colour, int nmr, int x_zero,
+                                                int *status, int jb, int rr)
 {
     using SL = Staged<GA>;
     using SC = StagedC<CL>;
@@ -507,7 +601,7 @@ __device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, cons
     if (!x_zero) {
         Cx<float> cx[12];
         xx.load(i, xs);
-        if (JAC) {
+        if (MODE == SAP_JAC) {
             Cs.mul(l, acc, cx);  // C^-1 H x
 #pragma unroll
             for (int k = 0; k < 12; ++k)
@@ -536,9 +630,90 @@ __device__ __forceinline__ void sap_staged_body(const Geom &g, const SP &b, cons
     }
     __syncthreads();
 
+    // 2''. even-odd preconditioned MR (C^-1 of the odd sites from global memory)
+    if (MODE == SAP_EO) {
+        const bool even = l < (vb >> 1);
+        Cx<float> rho[12], t[12], ee[12];
+        auto hops = [&]() {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k] = Cx<float>{0.f, 0.f};
+            staged_hop_dir<0>(Us, l, nf[0], nb[0], rs, vb, acc);
+            staged_hop_dir<1>(Us, l, nf[1], nb[1], rs, vb, acc);
+            staged_hop_dir<2>(Us, l, nf[2], nb[2], rs, vb, acc);
+            staged_hop_dir<3>(Us, l, nf[3], nb[3], rs, vb, acc);
+        };
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ee[k] = Cx<float>{0.f, 0.f};
+        if (!even) {
+            clover_site(Ci, i, rv, t);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rs[k * vb + l] = t[k];
+        }
+        __syncthreads();
+        if (even) {
+            hops();
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                rho[k] = Cx<float>{fmaf(kappa, acc[k].r, rv[k].r), fmaf(kappa, acc[k].i, rv[k].i)};
+        }
+        __syncthreads();
+        if (even)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rs[k * vb + l] = rho[k];
+        __syncthreads();
+        for (int it = 0; it < nmr; ++it) {
+            if (!even) {
+                hops();
+#pragma unroll
+                for (int k = 0; k < 12; ++k) acc[k] = kappa * acc[k];
+                clover_site(Ci, i, acc, t);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) rs[k * vb + l] = t[k];
+            }
+            __syncthreads();
+            float pr = 0.f, pi = 0.f, pp = 0.f;
+            Cx<float> p[12];
+            if (even) {
+                hops();
+                Cs.mul(l, rho, p);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    p[k] = Cx<float>{fmaf(-kappa, acc[k].r, p[k].r), fmaf(-kappa, acc[k].i, p[k].i)};
+                    pr = fmaf(p[k].r, rho[k].r, fmaf(p[k].i, rho[k].i, pr));
+                    pi = fmaf(p[k].r, rho[k].i, fmaf(-p[k].i, rho[k].r, pi));
+                    pp = fmaf(p[k].r, p[k].r, fmaf(p[k].i, p[k].i, pp));
+                }
+            }
+            block_sum3(pr, pi, pp, red);
+            const Cx<float> alpha = (pp > 0.f) ? Cx<float>{pr / pp, pi / pp} : Cx<float>{0.f, 0.f};
+            if (even)
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    ee[k] = cfma(alpha, rho[k], ee[k]);
+                    rho[k] = rho[k] - alpha * p[k];
+                    rs[k * vb + l] = rho[k];
+                }
+            __syncthreads();
+        }
+        if (even)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rs[k * vb + l] = ee[k];
+        __syncthreads();
+        if (!even) {
+            hops();
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                t[k] = Cx<float>{fmaf(kappa, acc[k].r, rv[k].r), fmaf(kappa, acc[k].i, rv[k].i)};
+            clover_site(Ci, i, t, ee);
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) es[k * vb + l] = ee[k];
+        nmr = 0;
+    }
+
     // 2'. Jacobi on A_B with e in shared memory (rs): e_1 = r_B, then
     // e <- r_B + kappa C^-1 H_B e
-    if (JAC) {
+    if (MODE == SAP_JAC) {
         for (int it = 1; it < nmr; ++it) {
 #pragma unroll
             for (int k = 0; k < 12; ++k) acc[k] = Cx<float>{0.f, 0.f};
@@ -881,8 +1056,8 @@ static int sap_run_h16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clo
 }
 
 // FP16 storage: the compile-time kernel for cubic 2^4 and 4^4 domains
-template <bool JAC, class SP, class GA, class CL>
-static int sap_run_staged(const mgc_clover_s *op, SP b, SP x, GA U, CL C, int nrhs, int n_cy, int n_mr,
+template <int MODE, class SP, class GA, class CL>
+static int sap_run_staged(const mgc_clover_s *op, SP b, SP x, GA U, CL C, CL Ci, int nrhs, int n_cy, int n_mr,
                           int x_is_zero, cudaStream_t s, int prec, int compress);
 
 template <bool JAC, class GA>
@@ -893,7 +1068,7 @@ static int sap_dispatch16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, 
     const bool cube = g.lb[0] == g.lb[1] && g.lb[1] == g.lb[2] && g.lb[2] == g.lb[3];
     if (cube && g.lvb == 8) return sap_run_h16<JAC, 8>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, compress);
     if (cube && g.lvb == 4) return sap_run_h16<JAC, 4>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, compress);
-    return sap_run_staged<JAC>(op, b, x, U, C, nrhs, n_cy, n_mr, x_is_zero, s, 16, compress);
+    return sap_run_staged<JAC ? SAP_JAC : SAP_MR>(op, b, x, U, C, C, nrhs, n_cy, n_mr, x_is_zero, s, 16, compress);
 }
 
 // ------------------------------------------------------------------ batches of lattices
@@ -947,7 +1122,7 @@ __global__ void __launch_bounds__(256, 1) k_sap_staged_batch(SapBatch<SP, GA, CL
 {
     int k, jb, rr;
     batch_item(B, k, jb, rr);
-    sap_staged_body<false>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
+    sap_staged_body<SAP_MR>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
 }
 
 template <class SP, class GA, class CL>
@@ -1089,92 +1264,108 @@ int selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, cudaStr
     return h ? fail(MGC_ERR_TIMEOUT, "the self-test wait ran out as designed") : MGC_OK;
 }
 
-template <bool JAC, class SP, class GA, class CL>
-static int sap_run_staged(const mgc_clover_s *op, SP b, SP x, GA U, CL C, int nrhs, int n_cy, int n_mr,
+template <int MODE, class SP, class GA, class CL>
+static int sap_run_staged(const mgc_clover_s *op, SP b, SP x, GA U, CL C, CL Ci, int nrhs, int n_cy, int n_mr,
                           int x_is_zero, cudaStream_t s, int prec, int compress)
 {
     const Geom &g = op->gauge->lat->g;
     const int vb = 1 << g.lvb;
     const size_t smem = staged_smem<GA, CL>(vb);
-    auto kern = k_sap_staged<JAC, SP, GA, CL>;
+    auto kern = k_sap_staged<MODE, SP, GA, CL>;
     MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(g.nblocks / 2, nrhs);
     for (int cy = 0; cy < n_cy; ++cy)
         for (int colour = 0; colour < 2; ++colour) {
             const int xz = (cy == 0 && colour == 0) ? x_is_zero : 0;
-            kern<<<grid, vb, smem, s>>>(g, b, x, U, C, (float)op->kappa, colour, n_mr, xz, op->d_status);
+            kern<<<grid, vb, smem, s>>>(g, b, x, U, C, Ci, (float)op->kappa, colour, n_mr, xz, op->d_status);
             count(1, sap_launch_bytes(g, prec, compress, nrhs, xz != 0));
         }
     MGC_CUDA(cudaGetLastError());
     return MGC_OK;
 }
 
-template <bool JAC, class SP, class GA, class CL>
-static int sap_run(const Geom &g, SP b, SP x, GA U, CL C, double kappa, int nrhs, int n_cy, int n_mr, int x_is_zero,
+template <int MODE, class SP, class GA, class CL>
+static int sap_run(const Geom &g, SP b, SP x, GA U, CL C, CL Ci, double kappa, int nrhs, int n_cy, int n_mr,
+                   int x_is_zero,
                    cudaStream_t s, int prec, int compress)
 {
     using T = typename SP::Real;
     const int vb = 1 << g.lvb;
     const size_t smem = (size_t)vb * 12 * sizeof(Cx<T>) + 96 * sizeof(T);
-    auto kern = k_sap_colour<JAC, SP, GA, CL>;
+    auto kern = k_sap_colour<MODE, SP, GA, CL>;
     if (smem > 48 * 1024) MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(g.nblocks / 2, nrhs);
     for (int cy = 0; cy < n_cy; ++cy)
         for (int colour = 0; colour < 2; ++colour) {
             const int xz = (cy == 0 && colour == 0) ? x_is_zero : 0;
-            kern<<<grid, vb, smem, s>>>(g, b, x, U, C, (T)kappa, colour, n_mr, xz);
+            kern<<<grid, vb, smem, s>>>(g, b, x, U, C, Ci, (T)kappa, colour, n_mr, xz);
             count(1, sap_launch_bytes(g, prec, compress, nrhs, xz != 0));
         }
     MGC_CUDA(cudaGetLastError());
     return MGC_OK;
 }
 
-// the smoother for D (JAC = false: clover C, MR) or for A = C^-1 D (JAC = true:
-// clover C^-1, Jacobi)
-template <bool JAC>
+// the smoother: MR on D_B (clover C), Jacobi on A_B (clover C^-1) or even-odd
+// MR on D_B (clover C, odd-site C^-1 from global memory)
+template <int MODE>
 static int sap_launch_impl(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_it,
                            int x_is_zero, cudaStream_t s)
 {
     const mgc_gauge_s *ga = op->gauge;
     const Geom &g = ga->lat->g;
+    constexpr bool jac = MODE == SAP_JAC;
     if ((1 << g.lvb) > 256) return fail(MGC_ERR_UNSUPPORTED_SHAPE, "SAP domains are limited to 256 sites");
     if (prec == 64) {
-        return sap_run<JAC>(g, Spinor64{(double2 *)b, g.lvb}, Spinor64{(double2 *)x, g.lvb}, Gauge64{ga->U64, g.lvb},
-                            Clover64{JAC ? op->Ci64 : op->C64, g.lvb}, op->kappa, nrhs, n_cy, n_it, x_is_zero, s, prec,
-                            ga->compress);
+        return sap_run<MODE>(g, Spinor64{(double2 *)b, g.lvb}, Spinor64{(double2 *)x, g.lvb}, Gauge64{ga->U64, g.lvb},
+                             Clover64{jac ? op->Ci64 : op->C64, g.lvb}, Clover64{op->Ci64, g.lvb}, op->kappa, nrhs,
+                             n_cy, n_it, x_is_zero, s, prec, ga->compress);
     }
     if (!has_prec(ga, prec)) return fail(MGC_ERR_INVALID_ARG, "no copy of the operator at this precision");
     const int cp = ga->compress;
     if (prec == 32) {
         Spinor32 B{(float4 *)b, g.lvb}, X{(float4 *)x, g.lvb};
-        Clover32 C{(float4 *)(JAC ? op->Ci32 : op->C32), g.lvb};
+        Clover32 C{(float4 *)(jac ? op->Ci32 : op->C32), g.lvb}, Ci{(float4 *)op->Ci32, g.lvb};
         if (cp == 12)
-            return sap_run_staged<JAC>(op, B, X, Gauge32x12{(float4 *)ga->U32, g.lvb}, C, nrhs, n_cy, n_it, x_is_zero,
-                                       s, prec, cp);
-        return sap_run_staged<JAC>(op, B, X, Gauge32x18{(float2 *)ga->U32, g.lvb}, C, nrhs, n_cy, n_it, x_is_zero, s,
-                                   prec, cp);
+            return sap_run_staged<MODE>(op, B, X, Gauge32x12{(float4 *)ga->U32, g.lvb}, C, Ci, nrhs, n_cy, n_it,
+                                        x_is_zero, s, prec, cp);
+        return sap_run_staged<MODE>(op, B, X, Gauge32x18{(float2 *)ga->U32, g.lvb}, C, Ci, nrhs, n_cy, n_it,
+                                    x_is_zero, s, prec, cp);
     }
     const size_t nV = (size_t)nrhs * g.V;
     Spinor16 B{(uint4 *)b, (float *)((uint4 *)b + nV * 3), g.lvb};
     Spinor16 X{(uint4 *)x, (float *)((uint4 *)x + nV * 3), g.lvb};
-    Clover16 C = JAC ? Clover16{(uint4 *)op->Ci16, op->Ci16_sc, g.lvb} : Clover16{(uint4 *)op->C16, op->C16_sc, g.lvb};
+    const Clover16 Ci{(uint4 *)op->Ci16, op->Ci16_sc, g.lvb};
+    const Clover16 C = jac ? Ci : Clover16{(uint4 *)op->C16, op->C16_sc, g.lvb};
+    if (MODE == SAP_EO) {
+        if (cp == 12)
+            return sap_run_staged<SAP_EO>(op, B, X, Gauge16x12{(uint2 *)ga->U16, g.lvb}, C, Ci, nrhs, n_cy, n_it,
+                                          x_is_zero, s, 16, cp);
+        return sap_run_staged<SAP_EO>(op, B, X, Gauge16x18{(uint32_t *)ga->U16, g.lvb}, C, Ci, nrhs, n_cy, n_it,
+                                      x_is_zero, s, 16, cp);
+    }
     if (cp == 12)
-        return sap_dispatch16<JAC>(op, B, X, Gauge16x12{(uint2 *)ga->U16, g.lvb}, C, nrhs, n_cy, n_it, x_is_zero, s,
+        return sap_dispatch16<jac>(op, B, X, Gauge16x12{(uint2 *)ga->U16, g.lvb}, C, nrhs, n_cy, n_it, x_is_zero, s,
                                    cp);
-    return sap_dispatch16<JAC>(op, B, X, Gauge16x18{(uint32_t *)ga->U16, g.lvb}, C, nrhs, n_cy, n_it, x_is_zero, s,
+    return sap_dispatch16<jac>(op, B, X, Gauge16x18{(uint32_t *)ga->U16, g.lvb}, C, nrhs, n_cy, n_it, x_is_zero, s,
                                cp);
 }
 
 int launch_sap(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_mr, int x_is_zero,
                cudaStream_t s)
 {
-    return sap_launch_impl<false>(op, prec, b, x, nrhs, n_cy, n_mr, x_is_zero, s);
+    return sap_launch_impl<SAP_MR>(op, prec, b, x, nrhs, n_cy, n_mr, x_is_zero, s);
 }
 
 int launch_sap_A(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_jacobi,
                  int x_is_zero, cudaStream_t s)
 {
-    return sap_launch_impl<true>(op, prec, b, x, nrhs, n_cy, n_jacobi, x_is_zero, s);
+    return sap_launch_impl<SAP_JAC>(op, prec, b, x, nrhs, n_cy, n_jacobi, x_is_zero, s);
+}
+
+int launch_sap_eo(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_mr,
+                  int x_is_zero, cudaStream_t s)
+{
+    return sap_launch_impl<SAP_EO>(op, prec, b, x, nrhs, n_cy, n_mr, x_is_zero, s);
 }
 
 }  // namespace mgc

@@ -275,6 +275,13 @@ static int ensure_work(mgc_clover_s *op, int method, int m, int lowprec)
     return MGC_OK;
 }
 
+// the smoother as preconditioner (x = 0 on entry), with the domain solver p->sap_solver
+static int run_sap(mgc_clover_s *op, const mgc_solve_params *p, int prec, const void *v, void *z, cudaStream_t s)
+{
+    if (p->sap_solver == 2) return launch_sap_eo(op, prec, v, z, 1, p->n_cy, p->n_mr, 1, s);
+    return launch_sap(op, prec, v, z, 1, p->n_cy, p->n_mr, 1, s);
+}
+
 // read one device scalar (synchronises the stream)
 static int read_scalar(SolverWork *W, int slot, double *out, cudaStream_t s)
 {
@@ -296,11 +303,11 @@ static int precondition(mgc_clover_s *op, const mgc_solve_params *p, const doubl
     }
     if (p->smoother_prec == 64) {
         MGC_CUDA(cudaMemsetAsync(z, 0, spinor_bytes(g, 64, 1), s));
-        return launch_sap(op, 64, v, z, 1, p->n_cy, p->n_mr, 1, s);
+        return run_sap(op, p, 64, v, z, s);
     }
     MGC_TRY(launch_convert(g, 1, 64, v, p->smoother_prec, W->rl, s));
     MGC_CUDA(cudaMemsetAsync(W->zl, 0, spinor_bytes(g, p->smoother_prec, 1), s));
-    MGC_TRY(launch_sap(op, p->smoother_prec, W->rl, W->zl, 1, p->n_cy, p->n_mr, 1, s));
+    MGC_TRY(run_sap(op, p, p->smoother_prec, W->rl, W->zl, s));
     return launch_convert(g, 1, p->smoother_prec, W->zl, 64, z, s);
 }
 
@@ -821,11 +828,11 @@ static int precondition32(mgc_clover_s *op, const mgc_solve_params *p, const flo
     }
     if (p->smoother_prec == 32) {
         MGC_CUDA(cudaMemsetAsync(z, 0, spinor_bytes(g, 32, 1), s));
-        return launch_sap(op, 32, v, z, 1, p->n_cy, p->n_mr, 1, s);
+        return run_sap(op, p, 32, v, z, s);
     }
     MGC_TRY(launch_convert(g, 1, 32, v, 16, W->rl, s));
     MGC_CUDA(cudaMemsetAsync(W->zl, 0, spinor_bytes(g, 16, 1), s));
-    MGC_TRY(launch_sap(op, 16, W->rl, W->zl, 1, p->n_cy, p->n_mr, 1, s));
+    MGC_TRY(run_sap(op, p, 16, W->rl, W->zl, s));
     return launch_convert(g, 1, 16, W->zl, 32, z, s);
 }
 
@@ -1208,6 +1215,7 @@ static int check_params(const mgc_clover_s *op, const mgc_solve_params *p)
     if (p->method == 3 && (p->precond != 1 || p->smoother_prec == 64 || !has_prec(op->gauge, 32)))
         return fail(MGC_ERR_INVALID_ARG, "the QWS solve needs an FP32 copy, precond 1 and a 32- or 16-bit smoother");
     if (p->precond != 0 && p->precond != 1) return fail(MGC_ERR_INVALID_ARG, "precond must be 0 or 1");
+    if (p->sap_solver != 0 && p->sap_solver != 2) return fail(MGC_ERR_INVALID_ARG, "sap_solver must be 0 or 2");
     if (p->precond == 1 && !has_prec(op->gauge, p->smoother_prec))
         return fail(MGC_ERR_INVALID_ARG, "no copy of the operator at smoother_prec");
     if (p->method == 2 && (!has_prec(op->gauge, 32) || (p->precond == 1 && p->smoother_prec == 64)))
