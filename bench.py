@@ -649,11 +649,38 @@ def main():
             a1.record(stream)
             a1.synchronize()
             sa.append(a0.elapsed_time(a1))
+        # the default method with even-odd preconditioned MR domain solves in the smoother
+        peo = api.solve_params(method=2, precond=1, smoother_prec=w["prec"], n_cy=w["n_cy"], n_mr=w["n_mr"],
+                               restart=w["restart"], tol=w["tol"], max_iter=500, inner_tol=w["inner_tol"],
+                               sap_solver=2)
+        xe, ie = op.solve(b, peo)
+        torch.cuda.synchronize()
+        q0.record(stream)
+        for _ in range(nq):
+            xe, ie = op.solve(b, peo)
+            if ie.status != 0 or ie.true_res > w["tol"]:
+                raise RuntimeError(f"even-odd smoother solve failed: status {ie.status}")
+        q1.record(stream)
+        q1.synchronize()
+        t_eo = q0.elapsed_time(q1) / 1e3 / nq
+        se = []
+        for _ in range(reps):
+            zl.zero_()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            op.sap_smooth_eo(rl, zl, w["prec"], 1, w["n_cy"], w["n_mr"], x_is_zero=True)
+            a1.record(stream)
+            a1.synchronize()
+            se.append(a0.elapsed_time(a1))
+        counters(lib, reset=True)
+        eo = {"method": "the default two-level solve with even-odd preconditioned MR domain solves",
+              "ms": 1e3 * t_eo, "inner_iters": ie.iters, "true_residual": ie.true_res,
+              "sap_eo_launch_us": 1e3 * statistics.median(se) / launches_per_call}
         qws = {"method": "QWS (Sec. 2): FP64 Richardson around FP32 BiCGStab on A M_SAP, A = C^-1 D, "
                          f"SAP for A with {w['n_mr']} Jacobi iterations per domain",
                "ms": 1e3 * t_q, "bicgstab_iters": iq.iters, "true_residual": iq.true_res,
                "gbs": nbq / nq / t_q / 1e9, "launches": nlq // nq,
-               "sap_A_launch_us": 1e3 * statistics.median(sa) / launches_per_call}
+               "sap_A_launch_us": 1e3 * statistics.median(sa) / launches_per_call, "even_odd_smoother": eo}
         counters(lib, reset=True)
 
     # ---------------- batched workload and link force (reported beside the headline)

@@ -160,3 +160,18 @@ def test_multigrid_rejects_bad_shapes():
     op64 = api.CloverOperator(api.Gauge(lat64, torch.from_numpy(U).cuda(), storage_prec=64), KAPPA, CSW)
     with pytest.raises(MgcError):
         api.Multigrid(op64, (4, 4, 4, 4), 4)
+
+
+def test_dependent_null_vectors_are_reported():
+    """Null vectors that are linearly dependent on an aggregate cannot be
+    orthonormalised: the basis build returns MGC_ERR_BREAKDOWN."""
+    from paper_2112_00501_gb300 import api
+    from paper_2112_00501_gb300._lib import MgcError
+
+    dims, block, agg, U, Cl, Ci, lat, op = _setup("4^4/2^4")
+    V = synth.gaussian_spinor(dims, 50, nrhs=3)
+    V[2] = V[0]
+    mg = api.Multigrid(op, agg, 3)
+    with pytest.raises(MgcError) as e:
+        mg.set_vectors(torch.from_numpy(V).cuda())
+    assert e.value.status == 6
