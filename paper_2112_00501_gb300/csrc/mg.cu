@@ -187,7 +187,9 @@ __global__ void k_prolong(MgGeom m, const float4 *W, const float2 *u, float4 *v,
 // ------------------------------------------------------------------ block Gram-Schmidt
 // For every (aggregate, chirality), W_i -= <W_j, W_i> W_j (j < i), then W_i /= |W_i|,
 // restricted to the aggregate and chirality; one thread block per
-// (aggregate, chirality), one thread per domain site; *bad counts zero norms.
+// (aggregate, chirality), one thread per domain site.  *bad counts the
+// restrictions left with less than 1e-5 of their norm after the projections
+// (linearly dependent to FP32 accuracy).
 __device__ __forceinline__ float2 block_sum2(float a, float b, float *red)
 {
     a = warp_sum(a);
@@ -214,8 +216,21 @@ __global__ void k_block_gs(MgGeom m, float4 *W, int *bad)
     const size_t fs = (size_t)m.g.V * 6;
     int ac[4];
     coarse_coords(m, a, ac);
+    auto norm2 = [&](const float4 *wi) {
+        float n2 = 0.f, dummy = 0.f;
+        for (int d = 0; d < m.da; ++d) {
+            const int s = (agg_domain(m, ac, d) << m.g.lvb) | l;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float4 t = *plane(wi, m.g, s, 3 * chi + q);
+                n2 = fmaf(t.x, t.x, fmaf(t.y, t.y, fmaf(t.z, t.z, fmaf(t.w, t.w, n2))));
+            }
+        }
+        return block_sum2(n2, dummy, red).x;
+    };
     for (int i = 0; i < m.nvec; ++i) {
         float4 *wi = W + i * fs;
+        const float n0 = norm2(wi);
         for (int j = 0; j < i; ++j) {
             const float4 *wj = W + j * fs;
             float re = 0.f, im = 0.f;
@@ -241,17 +256,8 @@ __global__ void k_block_gs(MgGeom m, float4 *W, int *bad)
                 }
             }
         }
-        float n2 = 0.f, dummy = 0.f;
-        for (int d = 0; d < m.da; ++d) {
-            const int s = (agg_domain(m, ac, d) << m.g.lvb) | l;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const float4 t = *plane(wi, m.g, s, 3 * chi + q);
-                n2 = fmaf(t.x, t.x, fmaf(t.y, t.y, fmaf(t.z, t.z, fmaf(t.w, t.w, n2))));
-            }
-        }
-        const float nn = block_sum2(n2, dummy, red).x;
-        if (!(nn > 0.f)) {
+        const float nn = norm2(wi);
+        if (!(nn > 1e-10f * n0)) {
             if (l == 0) atomicAdd(bad, 1);
             continue;
         }
