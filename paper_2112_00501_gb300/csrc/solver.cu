@@ -742,20 +742,23 @@ __global__ void __launch_bounds__(RT) k_map32(long long n4, F f)
 template <class K>
 static int grid32(K kern, long long n4)
 {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
+    // per device (SM counts may differ), per kernel instantiation
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &c = cached[dev >= 0 && dev < 64 ? dev : 0];
+    if (!c) {
+        int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, RT, 0);
         if (sms < 1) sms = 1;
         if (per < 1) per = 1;
         while (per > 1 && sms * per > RGRID_MAX) --per;
-        cached = sms * per > RGRID_MAX ? RGRID_MAX : sms * per;
+        c = sms * per > RGRID_MAX ? RGRID_MAX : sms * per;
     }
     long long need = (n4 + (long long)RT * U4 - 1) / ((long long)RT * U4);
     if (need < 1) need = 1;
-    return need < cached ? (int)need : cached;
+    return need < c ? (int)need : c;
 }
 
 // n: complex entries (even); f takes a float4 index
