@@ -434,9 +434,13 @@ def profile_kernel(which):
                                       compress=w["compress"]), w["kappa"], w["csw"])
     bp = lat.pack(b, w["prec"])
     xp = lat.zeros_packed(w["prec"])
+    if which == "dslash64":
+        bp, xp = lat.pack(b, 64), lat.empty_packed(64)
     for _ in range(2):
         if which == "sap":
             op.sap_smooth(bp, xp, w["prec"], 1, 1, w["n_mr"], x_is_zero=False)
+        elif which == "dslash64":
+            op.apply_D(bp, 64, 1, xp)
         else:
             op.apply_D(bp, w["prec"], 1, xp)
     torch.cuda.synchronize()
@@ -457,7 +461,7 @@ def main():
     ap.add_argument("--no-force", action="store_true")
     ap.add_argument("--no-qws", action="store_true")
     ap.add_argument("--no-mg", action="store_true")
-    ap.add_argument("--profile-kernel", choices=["sap", "dslash"], default=None,
+    ap.add_argument("--profile-kernel", choices=["sap", "dslash", "dslash64"], default=None,
                     help="run only a few launches of one kernel on 24^3x48 (for ncu captures)")
     args = ap.parse_args()
     if args.profile_kernel:
