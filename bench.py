@@ -38,9 +38,9 @@ WORKLOAD = dict(name="32^3x64", dims=(32, 32, 32, 64), block=(4, 4, 4, 4), eps=0
 CPU_SAMPLE_DIMS = (16, 16, 16, 8)
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
 # DRAM bytes (read + write) of one k_sap_h16 colour launch per lattice site,
-# from an ncu capture on 24^3 x 48 (164,190,464 B / 663,552 sites); the
+# from an ncu capture on 24^3 x 48 (164,292,096 B / 663,552 sites); the
 # kernel's traffic is per domain, so it scales with the sites
-SAP_H16_DRAM_BYTES_PER_SITE = 164190464.0 / 663552
+SAP_H16_DRAM_BYTES_PER_SITE = 164292096.0 / 663552
 # conventional flop counts per site: hopping 1320, clover 504, kappa axpy 48
 FLOP_D = 1872.0
 
