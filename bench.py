@@ -601,6 +601,7 @@ def main():
         return t, by / n
 
     t_d16, by_d16 = time_dslash(w["prec"])
+    t_d32, by_d32 = time_dslash(32)
     t_d64, by_d64 = time_dslash(64)
 
     # ---------------- plain FP64 GPU path for the time-to-solution comparison
@@ -727,6 +728,8 @@ def main():
         "fp64_path": fp64,
         "mixed_over_fp64_speedup": (fp64["ms"] / (1e3 * t_max / args.steps)) if fp64 else None,
         "dslash": {"fp16_12real_gbs": by_d16 / t_d16 / 1e9, "fp16_us": 1e6 * t_d16,
+                   "fp32_12real_gbs": by_d32 / t_d32 / 1e9, "fp32_us": 1e6 * t_d32,
+                   "fp32_frac_hbm": (by_d32 / t_d32 / 1e9 / hbm) if hbm else None,
                    "fp64_gbs": by_d64 / t_d64 / 1e9, "fp64_us": 1e6 * t_d64,
                    "fp16_frac_hbm": (by_d16 / t_d16 / 1e9 / hbm) if hbm else None},
         "sap_sweep": {"launch_us": 1e6 * t_launch, "algorithmic_gbs": bytes_launch / t_launch / 1e9,
