@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256, (LVB > 0 && sizeof(typename SP::Real) == 
     int c[4];
     site_coords(gg, i, c);
     Cx<T> o[12];
-    dirac_site<DAG>(gg, c, i, src, Ug, Cg, kappa, o);
+    dirac_site_k<DAG>(gg, c, i, src, Ug, Cg, kappa, o);
     dst.store(i, o);
 }
 

@@ -72,17 +72,17 @@ __global__ void __launch_bounds__(256, 1) k_dirac_batch(DiracBatch<SP, GA, CL> B
     int c[4];
     site_coords(gg, i, c);
     Cx<T> acc[RB][12];
-    hop_site_multi<DAG, RB>(gg, c, i, src, nr, Ug, acc);
     const T kappa = B.kappa[k];
+    hop_site_multi<DAG, RB>(gg, c, i, src, nr, Ug, -kappa, acc);
 #pragma unroll
     for (int q = 0; q < RB; ++q)
         if (q < nr) {
             Cx<T> psi[12], o[12];
-            src[q].load(i, psi);
-            clover_site(Cg, i, psi, o);
+            const T sp = load_s(src[q], i, psi);
+            const T sc = clover_site_s(Cg, i, psi, o) * sp;
 #pragma unroll
             for (int a = 0; a < 12; ++a)
-                o[a] = Cx<T>{fma(-kappa, acc[q][a].r, o[a].r), fma(-kappa, acc[q][a].i, o[a].i)};
+                o[a] = Cx<T>{fma(sc, o[a].r, acc[q][a].r), fma(sc, o[a].i, acc[q][a].i)};
             shift_rhs(base_out, r0 + q, gg.V).store(i, o);
         }
 }

@@ -32,6 +32,104 @@ __device__ __forceinline__ void load_project(const Spinor16 &in, int j, bool fli
     for (int k = 0; k < 6; ++k) h[k] = sc * h[k];
 }
 
+// ---- the operator kernels' form: every hop is accumulated with a real
+// coefficient by fused multiply-adds, the coefficient carrying -kappa, the
+// boundary sign and (FP16 spinors) the neighbour's per-site scale, so no
+// separate scaling or kappa multiplication is left
+
+// h = P psi(j) unscaled; returns the factor that restores psi's scale
+template <int MU, int SGN, class SP, typename T>
+__device__ __forceinline__ T load_project_s(const SP &in, int j, Cx<T> h[6])
+{
+    Cx<T> s[12];
+    in.load(j, s);
+    project<MU, SGN>(s, h);
+    return T(1);
+}
+template <int MU, int SGN>
+__device__ __forceinline__ float load_project_s(const Spinor16 &in, int j, Cx<float> h[6])
+{
+    Cx<float> s[12];
+    in.load_raw(j, s);
+    project<MU, SGN>(s, h);
+    return in.scale_of(j);
+}
+
+// psi(i) unscaled and its scale factor
+template <class SP, typename T>
+__device__ __forceinline__ T load_s(const SP &in, int i, Cx<T> psi[12])
+{
+    in.load(i, psi);
+    return T(1);
+}
+__device__ __forceinline__ float load_s(const Spinor16 &in, int i, Cx<float> psi[12])
+{
+    in.load_raw(i, psi);
+    return in.scale_of(i);
+}
+
+// out = C(i) psi unscaled; returns the clover's scale factor
+template <class CL, typename T>
+__device__ __forceinline__ T clover_site_s(const CL &C, int i, const Cx<T> psi[12], Cx<T> out[12])
+{
+    T cl[72];
+    C.load(i, cl);
+    clover_mul(cl, psi, out);
+    return T(1);
+}
+__device__ __forceinline__ float clover_site_s(const Clover16 &C, int i, const Cx<float> psi[12], Cx<float> out[12])
+{
+    float cl[72];
+    const float sc = C.load_raw(i, cl);
+    clover_mul(cl, psi, out);
+    return sc;
+}
+
+// acc += coef * (the four-spinor reconstructed from w)
+template <int MU, int SGN, typename T>
+__device__ __forceinline__ void reconstruct_fma(Cx<T> acc[12], const Cx<T> w[6], T coef)
+{
+    const T lo = (MU == 3 ? (SGN > 0 ? -coef : coef) : (SGN > 0 ? coef : -coef));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[c] = Cx<T>{fma(coef, w[c].r, acc[c].r), fma(coef, w[c].i, acc[c].i)};
+        acc[3 + c] = Cx<T>{fma(coef, w[3 + c].r, acc[3 + c].r), fma(coef, w[3 + c].i, acc[3 + c].i)};
+        Cx<T> o0, o1;
+        if (MU == 3) {
+            o0 = w[c];
+            o1 = w[3 + c];
+        } else {
+            isigma<MU>(w[c], w[3 + c], o0, o1);
+        }
+        acc[6 + c] = Cx<T>{fma(lo, o0.r, acc[6 + c].r), fma(lo, o0.i, acc[6 + c].i)};
+        acc[9 + c] = Cx<T>{fma(lo, o1.r, acc[9 + c].r), fma(lo, o1.i, acc[9 + c].i)};
+    }
+}
+
+// acc += mk * (the two hops along MU), mk = -kappa
+template <int MU, bool DAG, class SP, class GA, typename T>
+__device__ __forceinline__ void hop_dir_k(const Geom &g, const int c[4], int i, const SP &in, const GA &U, T mk,
+                                          Cx<T> acc[12])
+{
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    bool wr;
+    Cx<T> h[6], w[6], u[9];
+    int j = neighbour(g, c, MU, +1, &wr);
+    T coef = mk * load_project_s<MU, SF>(in, j, h);
+    if (MU == 3 && wr && g.tbc < 0) coef = -coef;
+    U.load(i, MU, u);
+    su3_mul(u, h, w);
+    reconstruct_fma<MU, SF>(acc, w, coef);
+
+    j = neighbour(g, c, MU, -1, &wr);
+    coef = mk * load_project_s<MU, SB>(in, j, h);
+    if (MU == 3 && wr && g.tbc < 0) coef = -coef;
+    U.load(j, MU, u);
+    su3_dag_mul(u, h, w);
+    reconstruct_fma<MU, SB>(acc, w, coef);
+}
+
 template <int MU, bool DAG, class SP, class GA, typename T>
 __device__ __forceinline__ void hop_dir(const Geom &g, const int c[4], int i, const SP &in, const GA &U,
                                         Cx<T> acc[12])
@@ -65,11 +163,12 @@ __device__ __forceinline__ void hop_site(const Geom &g, const int c[4], int i, c
     hop_dir<3, DAG>(g, c, i, in, U, acc);
 }
 
-// The hopping sums of RB right-hand sides at one site, each link loaded once
-// and applied to all of them; only the first nr (<= RB) are computed.
+// The hopping sums of RB right-hand sides at one site in the operator
+// kernels' form (coefficient mk = -kappa), each link loaded once and applied
+// to all of them; only the first nr (<= RB) are computed.
 template <int MU, bool DAG, int RB, class SP, class GA, typename T>
 __device__ __forceinline__ void hop_dir_multi(const Geom &g, const int c[4], int i, const SP (&in)[RB], int nr,
-                                              const GA &U, Cx<T> (&acc)[RB][12])
+                                              const GA &U, T mk, Cx<T> (&acc)[RB][12])
 {
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
@@ -81,9 +180,10 @@ __device__ __forceinline__ void hop_dir_multi(const Geom &g, const int c[4], int
 #pragma unroll
     for (int q = 0; q < RB; ++q)
         if (q < nr) {
-            load_project<MU, SF>(in[q], j, flip, h);
+            T coef = mk * load_project_s<MU, SF>(in[q], j, h);
+            if (flip) coef = -coef;
             su3_mul(u, h, w);
-            reconstruct_add<MU, SF>(acc[q], w);
+            reconstruct_fma<MU, SF>(acc[q], w, coef);
         }
     j = neighbour(g, c, MU, -1, &wr);
     flip = MU == 3 && wr && g.tbc < 0;
@@ -91,24 +191,25 @@ __device__ __forceinline__ void hop_dir_multi(const Geom &g, const int c[4], int
 #pragma unroll
     for (int q = 0; q < RB; ++q)
         if (q < nr) {
-            load_project<MU, SB>(in[q], j, flip, h);
+            T coef = mk * load_project_s<MU, SB>(in[q], j, h);
+            if (flip) coef = -coef;
             su3_dag_mul(u, h, w);
-            reconstruct_add<MU, SB>(acc[q], w);
+            reconstruct_fma<MU, SB>(acc[q], w, coef);
         }
 }
 
 template <bool DAG, int RB, class SP, class GA, typename T>
 __device__ __forceinline__ void hop_site_multi(const Geom &g, const int c[4], int i, const SP (&in)[RB], int nr,
-                                               const GA &U, Cx<T> (&acc)[RB][12])
+                                               const GA &U, T mk, Cx<T> (&acc)[RB][12])
 {
 #pragma unroll
     for (int q = 0; q < RB; ++q)
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[q][k] = Cx<T>{0, 0};
-    hop_dir_multi<0, DAG>(g, c, i, in, nr, U, acc);
-    hop_dir_multi<1, DAG>(g, c, i, in, nr, U, acc);
-    hop_dir_multi<2, DAG>(g, c, i, in, nr, U, acc);
-    hop_dir_multi<3, DAG>(g, c, i, in, nr, U, acc);
+    hop_dir_multi<0, DAG>(g, c, i, in, nr, U, mk, acc);
+    hop_dir_multi<1, DAG>(g, c, i, in, nr, U, mk, acc);
+    hop_dir_multi<2, DAG>(g, c, i, in, nr, U, mk, acc);
+    hop_dir_multi<3, DAG>(g, c, i, in, nr, U, mk, acc);
 }
 
 // out = C(i) psi
@@ -128,6 +229,26 @@ __device__ __forceinline__ void clover_site(const Clover16 &C, int i, const Cx<f
     clover_mul(cl, psi, out);
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[k] = sc * out[k];
+}
+
+// (D psi)(x) in the operator kernels' form: the hops accumulated with
+// -kappa (and the spinor scales) as coefficients, then C psi added with the
+// clover and spinor scales as one coefficient
+template <bool DAG, class SP, class GA, class CL, typename T>
+__device__ __forceinline__ void dirac_site_k(const Geom &g, const int c[4], int i, const SP &in, const GA &U,
+                                             const CL &C, T kappa, Cx<T> out[12])
+{
+    Cx<T> acc[12], psi[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = Cx<T>{0, 0};
+    hop_dir_k<0, DAG>(g, c, i, in, U, -kappa, acc);
+    hop_dir_k<1, DAG>(g, c, i, in, U, -kappa, acc);
+    hop_dir_k<2, DAG>(g, c, i, in, U, -kappa, acc);
+    hop_dir_k<3, DAG>(g, c, i, in, U, -kappa, acc);
+    const T sp = load_s(in, i, psi);
+    const T sc = clover_site_s(C, i, psi, out) * sp;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = Cx<T>{fma(sc, out[k].r, acc[k].r), fma(sc, out[k].i, acc[k].i)};
 }
 
 // (D psi)(x) = C(x) psi(x) - kappa * hop  at packed site i with coordinates c
