@@ -694,8 +694,13 @@ __device__ __forceinline__ void finish_reduce(double *acc, double (*sh)[RT / 32]
 // FP32 vectors are read as float4 (two complex entries per load).  Each thread
 // takes U4 independent float4 entries per step (grid stride apart, so a warp's
 // loads stay contiguous) to keep enough loads in flight to cover HBM latency;
-// its FP32 partial sums go to FP64 after every step (U4 calls = 2 U4 entries).
+// its FP32 partial sums go to FP64 every flush_steps<NV>() steps.  With many
+// sums (the Gram-Schmidt inner products) a flush per step made the kernel
+// FP64-bound on GB300 (NV conversions and additions per four entries), so
+// those flush every fourth step: an FP32 partial then holds 16 float4 entries.
 constexpr int U4 = 4;
+template <int NV>
+__host__ __device__ constexpr int flush_steps() { return NV >= 8 ? 4 : 1; }
 
 template <int NV, class F>
 __global__ void __launch_bounds__(RT) k_reduce32(long long n4, F f, double *partial, unsigned *counter, double *out)
@@ -711,13 +716,17 @@ __global__ void __launch_bounds__(RT) k_reduce32(long long n4, F f, double *part
     }
     const long long stride = (long long)gridDim.x * RT;
     long long e = (long long)blockIdx.x * RT + threadIdx.x;
+    int step = 0;
     for (; e + (U4 - 1) * stride < n4; e += U4 * stride) {
 #pragma unroll
         for (int u = 0; u < U4; ++u) f(e + u * stride, facc);
+        if (++step == flush_steps<NV>()) {
+            step = 0;
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            acc[k] += (double)facc[k];
-            facc[k] = 0.f;
+            for (int k = 0; k < NV; ++k) {
+                acc[k] += (double)facc[k];
+                facc[k] = 0.f;
+            }
         }
     }
     for (; e < n4; e += stride) f(e, facc);
