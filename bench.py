@@ -434,15 +434,17 @@ def profile_kernel(which):
                                       compress=w["compress"]), w["kappa"], w["csw"])
     bp = lat.pack(b, w["prec"])
     xp = lat.zeros_packed(w["prec"])
-    if which == "dslash64":
-        bp, xp = lat.pack(b, 64), lat.empty_packed(64)
+    prec = {"dslash64": 64, "dslash32": 32}.get(which, w["prec"])
+    if prec != w["prec"]:
+        bp, xp = lat.pack(b, prec), lat.empty_packed(prec)
+    if which == "dslash16x18":
+        op = api.CloverOperator(api.Gauge(lat, torch.from_numpy(U).cuda(), storage_prec=w["prec"], compress=18),
+                                w["kappa"], w["csw"])
     for _ in range(2):
         if which == "sap":
             op.sap_smooth(bp, xp, w["prec"], 1, 1, w["n_mr"], x_is_zero=False)
-        elif which == "dslash64":
-            op.apply_D(bp, 64, 1, xp)
         else:
-            op.apply_D(bp, w["prec"], 1, xp)
+            op.apply_D(bp, prec, 1, xp)
     torch.cuda.synchronize()
     print("profile run done")
     return 0
@@ -461,7 +463,8 @@ def main():
     ap.add_argument("--no-force", action="store_true")
     ap.add_argument("--no-qws", action="store_true")
     ap.add_argument("--no-mg", action="store_true")
-    ap.add_argument("--profile-kernel", choices=["sap", "dslash", "dslash64"], default=None,
+    ap.add_argument("--profile-kernel", choices=["sap", "dslash", "dslash32", "dslash16x18", "dslash64"],
+                    default=None,
                     help="run only a few launches of one kernel on 24^3x48 (for ncu captures)")
     args = ap.parse_args()
     if args.profile_kernel:
@@ -582,18 +585,18 @@ def main():
     sap_tflops = flops_call / (statistics.median(sap_ms) / 1e3) / 1e12
 
     # ---------------- Dslash alone (workload storage and FP64)
-    def time_dslash(prec):
+    def time_dslash(prec, dop=op):
         xin = lat.pack(b, prec)
         out = lat.empty_packed(prec)
         for _ in range(3):
-            op.apply_D(xin, prec, 1, out)
+            dop.apply_D(xin, prec, 1, out)
         torch.cuda.synchronize()
         counters(lib, reset=True)
         d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         n = 20
         d0.record(stream)
         for _ in range(n):
-            op.apply_D(xin, prec, 1, out)
+            dop.apply_D(xin, prec, 1, out)
         d1.record(stream)
         d1.synchronize()
         _, by = counters(lib, reset=True)
@@ -603,6 +606,11 @@ def main():
     t_d16, by_d16 = time_dslash(w["prec"])
     t_d32, by_d32 = time_dslash(32)
     t_d64, by_d64 = time_dslash(64)
+    # the FP16 operator with 18-real links: 48 B more per site, no row-2 rebuild
+    g18 = api.Gauge(lat, Ud, storage_prec=w["prec"], compress=18)
+    op18 = api.CloverOperator(g18, w["kappa"], w["csw"])
+    t_d16_18, by_d16_18 = time_dslash(w["prec"], op18)
+    del op18, g18
 
     # ---------------- plain FP64 GPU path for the time-to-solution comparison
     fp64 = None
@@ -731,7 +739,9 @@ def main():
                    "fp32_12real_gbs": by_d32 / t_d32 / 1e9, "fp32_us": 1e6 * t_d32,
                    "fp32_frac_hbm": (by_d32 / t_d32 / 1e9 / hbm) if hbm else None,
                    "fp64_gbs": by_d64 / t_d64 / 1e9, "fp64_us": 1e6 * t_d64,
-                   "fp16_frac_hbm": (by_d16 / t_d16 / 1e9 / hbm) if hbm else None},
+                   "fp16_frac_hbm": (by_d16 / t_d16 / 1e9 / hbm) if hbm else None,
+                   "fp16_18real_gbs": by_d16_18 / t_d16_18 / 1e9, "fp16_18real_us": 1e6 * t_d16_18,
+                   "fp16_18real_frac_hbm": (by_d16_18 / t_d16_18 / 1e9 / hbm) if hbm else None},
         "sap_sweep": {"launch_us": 1e6 * t_launch, "algorithmic_gbs": bytes_launch / t_launch / 1e9,
                       "frac_hbm": (bytes_launch / t_launch / 1e9 / hbm) if hbm else None,
                       "tflops_fp32": sap_tflops, "frac_fp32_peak": sap_tflops / FP32_FMA_PEAK_TFLOPS},
