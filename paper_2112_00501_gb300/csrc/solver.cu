@@ -852,8 +852,8 @@ typedef std::complex<double> zd;
 
 // inner FGCR on W->r32 (unit norm on entry, residual on exit); fills gamma for
 // the k directions it built; *rr_out = final ||r||^2
-static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_in, int max_it, int *k_out,
-                        std::vector<zd> &gamma, double *rr_out, cudaStream_t s)
+static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_in, double rr0, int max_it,
+                        int *k_out, std::vector<zd> &gamma, double *rr_out, cudaStream_t s)
 {
     SolverWork *W = op->work;
     const long long n = (long long)op->gauge->lat->g.V * 12;
@@ -863,21 +863,24 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
     std::vector<double> n2(m);
     std::vector<zd> alpha(m);
     std::vector<std::vector<zd>> R(m, std::vector<zd>(m, zd(0, 0)));
-    double rr = 1.0;
+    double rr = rr0;
     int k = 0;
     for (int j = 0; j < m; ++j) {
         float2 *zj = W->z32[j], *wj = W->w32[j];
         MGC_TRY(precondition32(op, p, r, zj, s));
         MGC_TRY(launch_dirac(op, 32, false, zj, wj, 1, s));
-        // d_i = <w'_i, w_j> (i < j) and rho = <w_j, r>, eight at a time
+        // d_i = <w'_i, w_j> (i < j) and rho = <w_j, r>, eight at a time, and
+        // ||w_j||^2 with the first eight
         std::vector<zd> d(j + 1);
+        double ww = 0.0;
         for (int i0 = 0; i0 <= j; i0 += 8) {
             const int cnt = (j + 1 - i0 < 8) ? j + 1 - i0 : 8;
+            const bool first = i0 == 0;
             // <L_q, w_j> with L = (w'_0 .. w'_{j-1}, r)
             PtrList4 L{};
             for (int q = 0; q < cnt; ++q) L.p[q] = (const float4 *)((i0 + q < j) ? W->w32[i0 + q] : r);
             const float4 *wv = (const float4 *)wj;
-            MGC_TRY(reduce32<16>(
+            MGC_TRY(reduce32<17>(
                 n,
                 [=] __device__(long long e, float *acc) {
                     const float4 v = wv[e];
@@ -888,23 +891,65 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
                             facc_dot(acc + 2 * q, lo2(a), lo2(v));
                             facc_dot(acc + 2 * q, hi2(a), hi2(v));
                         }
+                    if (first) {
+                        facc_n2(acc + 16, lo2(v));
+                        facc_n2(acc + 16, hi2(v));
+                    }
                 },
                 W, sc + S_BETA, s, 8.0 * n * (cnt + 1)));
-            double h[16];
-            MGC_TRY(read_scalars(W, S_BETA, 2 * cnt, h, s));
+            double h[17];
+            MGC_TRY(read_scalars(W, S_BETA, first ? 17 : 2 * cnt, h, s));
             for (int q = 0; q < cnt; ++q) d[i0 + q] = zd(h[2 * q], h[2 * q + 1]);
+            if (first) ww = h[16];
         }
         const zd rho = std::conj(d[j]);  // <w_j, r>
-        // w'_j = w_j - sum_i c_i w'_i, c_i = d_i / ||w'_i||^2; ||w'_j||^2
+        // w'_j = w_j - sum_i c_i w'_i, c_i = d_i / ||w'_i||^2
         CoefList C{};
         PtrList4 Lw{};
+        double nw_est = ww;  // ||w'_j||^2 = ||w_j||^2 - sum_i |d_i|^2 / ||w'_i||^2 (w'_i orthogonal)
         for (int i = 0; i < j; ++i) {
             const zd c = d[i] / n2[i];
             R[i][j] = c;
             C.c[i] = make_float2((float)c.real(), (float)c.imag());
             Lw.p[i] = (const float4 *)W->w32[i];
+            nw_est -= std::norm(d[i]) / n2[i];
         }
         float4 *wj4 = (float4 *)wj;
+        float4 *r4 = (float4 *)r;
+        if (!bad(ww) && nw_est > 1e-3 * ww) {
+            // one pass: orthogonalise w_j and update r with alpha from the
+            // estimate; the exact ||w'_j||^2 (for later coefficients) and
+            // ||r||^2 come back from the same pass
+            alpha[j] = rho / nw_est;
+            const float2 a = make_float2((float)alpha[j].real(), (float)alpha[j].imag());
+            MGC_TRY(reduce32<2>(
+                n,
+                [=] __device__(long long e, float *acc) {
+                    float4 v = wj4[e];
+#pragma unroll
+                    for (int i = 0; i < MAXM; ++i)
+                        if (i < j) csub4(v, C.c[i], Lw.p[i][e]);
+                    wj4[e] = v;
+                    facc_n2(acc, lo2(v));
+                    facc_n2(acc, hi2(v));
+                    float4 u = r4[e];
+                    csub4(u, a, v);
+                    r4[e] = u;
+                    facc_n2(acc + 1, lo2(u));
+                    facc_n2(acc + 1, hi2(u));
+                },
+                W, sc + S_BETA, s, 8.0 * n * (j + 4)));
+            double h2[2];
+            MGC_TRY(read_scalars(W, S_BETA, 2, h2, s));
+            if (bad(h2[0]) || h2[0] == 0.0) return fail(MGC_ERR_BREAKDOWN, "inner FGCR: zero or non-finite direction");
+            n2[j] = h2[0];
+            rr = h2[1];
+            k = j + 1;
+            if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "inner FGCR: non-finite residual");
+            if (rr <= tol_in * tol_in * rr0) break;
+            continue;
+        }
+        // strong cancellation in the estimate: orthogonalise, then update r
         MGC_TRY(reduce32<1>(
             n,
             [=] __device__(long long e, float *acc) {
@@ -923,7 +968,6 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
         n2[j] = nw;
         alpha[j] = rho / nw;
         const float2 a = make_float2((float)alpha[j].real(), (float)alpha[j].imag());
-        float4 *r4 = (float4 *)r;
         MGC_TRY(reduce32<1>(
             n,
             [=] __device__(long long e, float *acc) {
@@ -937,7 +981,7 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
         MGC_TRY(read_scalars(W, S_RR, 1, &rr, s));
         k = j + 1;
         if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "inner FGCR: non-finite residual");
-        if (rr <= tol_in * tol_in) break;
+        if (rr <= tol_in * tol_in * rr0) break;
     }
     gamma.assign(k, zd(0, 0));
     for (int i = k - 1; i >= 0; --i) {
@@ -950,31 +994,102 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
     return MGC_OK;
 }
 
+// r32 = b - t site by site (the FP64 and FP32 packed layouts differ; t may be
+// null: r32 = b), and ||b - t||^2 into a device scalar slot.  The FP64
+// residual itself is not kept: the inner solve only needs its FP32 copy, and
+// r32 is not normalised, since FP32 covers every residual this solve reaches
+// (down to tol ||b||).
+static int residual_to32(mgc_clover_s *op, const double2 *b, const double2 *t, float2 *r32, int slot, cudaStream_t s)
+{
+    SolverWork *W = op->work;
+    const Geom g = op->gauge->lat->g;
+    const Spinor64 B{const_cast<double2 *>(b), g.lvb}, T{const_cast<double2 *>(t), g.lvb};
+    const Spinor32 R{reinterpret_cast<float4 *>(r32), g.lvb};
+    const bool has_t = t != nullptr;
+    auto f = [=] __device__(long long i, double *acc) {
+        Cx<double> v[12];
+        Cx<float> w[12];
+        B.load((int)i, v);
+        if (has_t) {
+            Cx<double> u[12];
+            T.load((int)i, u);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v[k] = v[k] - u[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            w[k] = Cx<float>{(float)v[k].r, (float)v[k].i};
+            acc[0] = fma(v[k].r, v[k].r, fma(v[k].i, v[k].i, acc[0]));
+        }
+        R.store((int)i, w);
+    };
+    k_reduce<1><<<red_grid(g.V), RT, 0, s>>>((long long)g.V, f, W->partial, W->counter, W->scal + slot);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * ((has_t ? 2 : 1) * 192.0 + 96.0));
+    return MGC_OK;
+}
+
+// x += sum_j gamma_j z_j site by site: the sum in FP32 (its rounding is far
+// below the inner tolerance), the update of x in FP64
+static int axpy_sum32(mgc_clover_s *op, double2 *x, const PtrList4 &Lz, const CoefList &G, int k, cudaStream_t s)
+{
+    const Geom g = op->gauge->lat->g;
+    const Spinor64 X{x, g.lvb};
+    const int lvb = g.lvb;
+    auto f = [=] __device__(long long i) {
+        Cx<float> e[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) e[c] = Cx<float>{0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+            if (j < k) {
+                const Spinor32 Z{const_cast<float4 *>(Lz.p[j]), lvb};
+                Cx<float> z[12];
+                Z.load((int)i, z);
+                const Cx<float> gj = {G.c[j].x, G.c[j].y};
+#pragma unroll
+                for (int c = 0; c < 12; ++c) e[c] = cfma(gj, z[c], e[c]);
+            }
+        Cx<double> v[12];
+        X.load((int)i, v);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) v[c] = v[c] + Cx<double>{(double)e[c].r, (double)e[c].i};
+        X.store((int)i, v);
+    };
+    k_map<<<red_grid(g.V), RT, 0, s>>>((long long)g.V, f);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * (2 * 192.0 + 96.0 * k));
+    return MGC_OK;
+}
+
 static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
 {
     SolverWork *W = op->work;
     const long long n = (long long)op->gauge->lat->g.V * 12;
-    double2 *x = W->x, *r = W->r, *b = W->b, *t = W->t;
+    double2 *x = W->x, *b = W->b, *t = W->t;
     float2 *r32 = W->r32;
     double *sc = W->scal;
     double bb, rr;
-    MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, b[e]); }, W, sc + S_BB, s, 1));
-    MGC_TRY(read_scalar(W, S_BB, &bb, s));
     info->iters = 0;
     info->restarts = 0;
     info->true_res = 0;
-    if (bb == 0.0) {
-        MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
-        return MGC_OK;
-    }
     if (p->x_is_guess) {
+        MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, b[e]); }, W, sc + S_BB, s, 1));
+        MGC_TRY(read_scalar(W, S_BB, &bb, s));
+        if (bb == 0.0) {
+            MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+            return MGC_OK;
+        }
         MGC_TRY(apply_D64(op, x, t, s));
-        MGC_TRY(residual(op, r, b, t, S_RR, s));
+        MGC_TRY(residual_to32(op, b, t, r32, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
     } else {
+        // x = 0: r = b, and ||b||^2 from the same pass
         MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
-        MGC_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-        rr = bb;
+        MGC_TRY(residual_to32(op, b, nullptr, r32, S_RR, s));
+        MGC_TRY(read_scalar(W, S_RR, &rr, s));
+        bb = rr;
+        if (bb == 0.0) return MGC_OK;
     }
     const double tol2 = p->tol * p->tol * bb;
     int iters = 0;
@@ -983,8 +1098,6 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
         if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "defect correction: non-finite residual");
         if (rr <= tol2) return MGC_OK;
         if (iters >= p->max_iter) return MGC_NOT_CONVERGED;
-        // r32 = r / ||r|| (site by site: the FP64 and FP32 packed layouts differ)
-        MGC_TRY(launch_scale_to32(op->gauge->lat->g, r, r32, 1.0 / std::sqrt(rr), s));
         // the last pass only needs to reach tol ||b||
         double tin = p->inner_tol;
         const double need = 0.5 * p->tol * std::sqrt(bb / rr);
@@ -992,31 +1105,18 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
         int k = 0;
         double rri;
         std::vector<zd> gamma;
-        MGC_TRY(inner_fgcr32(op, p, tin, p->max_iter - iters, &k, gamma, &rri, s));
+        MGC_TRY(inner_fgcr32(op, p, tin, rr, p->max_iter - iters, &k, gamma, &rri, s));
         iters += k;
-        // e = sum_j gamma_j z_j in FP32 (into w32[0], free after the inner solve;
-        // its rounding is far below the inner tolerance), then x += ||r|| e
+        // x += e, e = sum_j gamma_j z_j
         PtrList4 Lz{};
         CoefList G{};
         for (int j = 0; j < k; ++j) {
             Lz.p[j] = (const float4 *)W->z32[j];
             G.c[j] = make_float2((float)gamma[j].real(), (float)gamma[j].imag());
         }
-        float2 *esum = W->w32[0];
-        float4 *esum4 = (float4 *)esum;
-        MGC_TRY(map32(
-            n,
-            [=] __device__(long long e) {
-                float4 acc4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int j = 0; j < MAXM; ++j)
-                    if (j < k) csub4(acc4, make_float2(-G.c[j].x, -G.c[j].y), Lz.p[j][e]);
-                esum4[e] = acc4;
-            },
-            s, 8.0 * n * (k + 1)));
-        MGC_TRY(launch_axpy_from32(op->gauge->lat->g, x, esum, std::sqrt(rr), 0.0, s));
+        MGC_TRY(axpy_sum32(op, x, Lz, G, k, s));
         MGC_TRY(apply_D64(op, x, t, s));
-        MGC_TRY(residual(op, r, b, t, S_RR, s));
+        MGC_TRY(residual_to32(op, b, t, r32, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
         info->iters = iters;
         info->restarts++;
