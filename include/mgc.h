@@ -266,7 +266,7 @@ int mgc_solve(mgc_clover_t op, const double *b, double *x, int nrhs, const mgc_s
  * device-wide synchronisation a cudaMalloc/cudaFree pair brings.  It solves
  * D x = b for one right-hand side with flexible BiCGStab (p->method must be 1)
  * and performs no cudaMalloc, cudaFree or other allocation: its workspace is a
- * file-scope device array of fixed size (about 10.4 MB, held by every GPU that
+ * file-scope device array of fixed size (about 10.5 MB, held by every GPU that
  * loads the library until the process exits), which limits the lattice to
  * MGC_NOALLOC_MAX_SITES sites; larger lattices return
  * MGC_ERR_UNSUPPORTED_SHAPE.  b and x are canonical complex128 device pointers

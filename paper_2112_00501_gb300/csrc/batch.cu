@@ -98,6 +98,7 @@ __device__ __forceinline__ void seg_range(const SegTab &t, int &s, long long &st
 template <int NV, bool F32, class F>
 __global__ void __launch_bounds__(BRT) k_seg_reduce(SegTab t, F f, double *partial)
 {
+    static_assert(NV <= 16, "the batch partial-sum area holds sixteen accumulators per block");
     __shared__ double sh[NV][BRT / 32];
     int s;
     long long start, end;

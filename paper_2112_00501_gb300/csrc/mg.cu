@@ -374,6 +374,7 @@ __global__ void k_coarse_apply(MgGeom m, const float2 *Dc, const float2 *u, floa
 template <int NV, class F>
 __global__ void __launch_bounds__(CRT) k_creduce(int n, F f, double *partial)
 {
+    static_assert(NV <= 4, "the coarse partial-sum area holds four accumulators per block");
     __shared__ double sh[NV][CRT / 32];
     double acc[NV];
 #pragma unroll

@@ -25,6 +25,9 @@ namespace mgc {
 
 constexpr int RT = 256;        // reduction threads per block
 constexpr int RGRID_MAX = 1024;
+// accumulators one reduction block may deposit: the partial-sum area holds
+// RGRID_MAX * PART_NV doubles, and every reduction template checks its width
+constexpr int PART_NV = 32;
 constexpr int MAXM = 32;
 
 struct SolverWork {
@@ -113,6 +116,7 @@ __device__ __forceinline__ void block_reduce(double *v, double (*sh)[RT / 32])
 template <int NV, class F>
 __global__ void __launch_bounds__(RT) k_reduce(long long n, F f, double *partial, unsigned *counter, double *out)
 {
+    static_assert(NV <= PART_NV, "more accumulators than the partial-sum area holds");
     __shared__ double sh[NV][RT / 32];
     __shared__ bool last;
     double acc[NV];
@@ -267,7 +271,7 @@ static int ensure_work(mgc_clover_s *op, int method, int m, int lowprec)
     }
     MGC_CUDA(cudaMalloc(&W->scal, S_TOTAL * sizeof(double)));
     MGC_CUDA(cudaMemset(W->scal, 0, S_TOTAL * sizeof(double)));
-    MGC_CUDA(cudaMalloc(&W->partial, RGRID_MAX * 16 * sizeof(double)));
+    MGC_CUDA(cudaMalloc(&W->partial, (size_t)RGRID_MAX * PART_NV * sizeof(double)));
     MGC_CUDA(cudaMalloc(&W->counter, sizeof(unsigned)));
     MGC_CUDA(cudaMemset(W->counter, 0, sizeof(unsigned)));
     MGC_CUDA(cudaMalloc(&W->stage, vb));
@@ -705,6 +709,7 @@ __host__ __device__ constexpr int flush_steps() { return NV >= 8 ? 4 : 1; }
 template <int NV, class F>
 __global__ void __launch_bounds__(RT) k_reduce32(long long n4, F f, double *partial, unsigned *counter, double *out)
 {
+    static_assert(NV <= PART_NV, "more accumulators than the partial-sum area holds");
     __shared__ double sh[NV][RT / 32];
     __shared__ bool last;
     double acc[NV];
@@ -1350,11 +1355,11 @@ static int run_method(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_inf
 // Scratch of mgc_solve_noalloc: a file-scope device array holding the
 // flexible BiCGStab workspace (x, r, b, t, four w and four z FP64 vectors, two
 // smoother buffers, reduction partials, scalars and the reduction ticket) for
-// lattices of up to MGC_NOALLOC_MAX_SITES sites, about 10.4 MB.  Every GPU
+// lattices of up to MGC_NOALLOC_MAX_SITES sites, about 10.5 MB.  Every GPU
 // that loads the library holds it until the process exits.
 constexpr size_t NA_VEC = (size_t)MGC_NOALLOC_MAX_SITES * 192;  // one FP64 packed spinor
 constexpr size_t NA_LOW = (size_t)MGC_NOALLOC_MAX_SITES * 96;   // one FP32 or FP16 packed spinor
-constexpr size_t NA_PART = (size_t)RGRID_MAX * 16 * sizeof(double);
+constexpr size_t NA_PART = (size_t)RGRID_MAX * PART_NV * sizeof(double);
 constexpr size_t NA_SCAL = 1024;  // >= S_TOTAL doubles
 constexpr size_t NA_CTR = 256;
 constexpr size_t NA_BYTES = 12 * NA_VEC + 2 * NA_LOW + NA_PART + NA_SCAL + NA_CTR;

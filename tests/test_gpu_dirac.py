@@ -101,10 +101,10 @@ def test_gauge_create_rejects_non_su3_for_12_real():
     api.Gauge(lat, torch.from_numpy(bad).cuda(), storage_prec=16, compress=18)
 
 
-@pytest.mark.parametrize("prec,compress", [(64, 18), (16, 12)])
+@pytest.mark.parametrize("prec,compress", [(64, 18), (32, 12), (16, 12), (16, 18)])
 def test_full_size_32c64_sampled_sites(prec, compress):
-    """32^3 x 64 at the benchmark's storage format, on 2048 sampled sites the
-    oracle computes one by one (its clover built on the fly)."""
+    """32^3 x 64 in each storage format the benchmark times, on 2048 sampled
+    sites the oracle computes one by one (its clover built on the fly)."""
     from paper_2112_00501_gb300 import synth
 
     name = "c2_32^3x64"
