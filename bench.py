@@ -203,7 +203,7 @@ def run_reference(args, rank, world):
 # storage, 12-real links, 4 x 4 SAP) as measured on the GPU path; converts the
 # oracle's site-iterations per second into the same unit when the reference
 # arm runs without a GPU measurement at hand (MGC_BYTES_PER_SITE_ITER overrides)
-BYTES_PER_SITE_ITER_DEFAULT = 4564.0
+BYTES_PER_SITE_ITER_DEFAULT = 4258.0
 
 
 # ---------------------------------------------------------------------- GPU side

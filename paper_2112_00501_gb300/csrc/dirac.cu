@@ -191,15 +191,19 @@ int launch_gauge_pack(const Geom &g, const double *canon_dev, int prec, int comp
 // 128-thread blocks, five per SM for FP32 arithmetic (96 registers, no
 // spills); measured against 256 x 2, 256 x 3 and 128 x 6 on 32^3 x 64.
 constexpr int DIRAC_THREADS = 128;
-template <bool DAG, int LVB, class SP, class GA, class CL>
-__global__ void __launch_bounds__(DIRAC_THREADS, (LVB > 0 && sizeof(typename SP::Real) == 4) ? 5 : 1)
-    k_dirac(Geom g, SP in, SP out, GA U, CL C, typename SP::Real kappa)
+// The input and output spinors may differ in storage (an FP16 input with the
+// FP32 operator); the arithmetic type is theirs, which must agree.
+template <bool DAG, int LVB, class SPI, class SPO, class GA, class CL>
+__global__ void __launch_bounds__(DIRAC_THREADS, (LVB > 0 && sizeof(typename SPI::Real) == 4) ? 5 : 1)
+    k_dirac(Geom g, SPI in, SPO out, GA U, CL C, typename SPI::Real kappa)
 {
-    using T = typename SP::Real;
+    using T = typename SPI::Real;
+    static_assert(std::is_same<T, typename SPO::Real>::value, "input and output share the arithmetic type");
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.V) return;
     const int r = blockIdx.y;
-    SP src = shift_rhs(in, r, g.V), dst = shift_rhs(out, r, g.V);
+    SPI src = shift_rhs(in, r, g.V);
+    SPO dst = shift_rhs(out, r, g.V);
     GA Ug = U;
     CL Cg = C;
     Geom gg = g;
@@ -216,17 +220,17 @@ __global__ void __launch_bounds__(DIRAC_THREADS, (LVB > 0 && sizeof(typename SP:
     dst.store(i, o);
 }
 
-template <int LVB, class SP, class GA, class CL>
-static void dirac_launch(const Geom &g, bool dag, SP in, SP out, GA U, CL C, double kappa, int nrhs, cudaStream_t s)
+template <int LVB, class SPI, class SPO, class GA, class CL>
+static void dirac_launch(const Geom &g, bool dag, SPI in, SPO out, GA U, CL C, double kappa, int nrhs, cudaStream_t s)
 {
-    using T = typename SP::Real;
+    using T = typename SPI::Real;
     dim3 grid(grid_for(g.V, DIRAC_THREADS), nrhs);
     if (dag) k_dirac<true, LVB><<<grid, DIRAC_THREADS, 0, s>>>(g, in, out, U, C, (T)kappa);
     else k_dirac<false, LVB><<<grid, DIRAC_THREADS, 0, s>>>(g, in, out, U, C, (T)kappa);
 }
 
-template <class SP, class GA, class CL>
-static void dirac_dispatch(const Geom &g, bool dag, SP in, SP out, GA U, CL C, double kappa, int nrhs,
+template <class SPI, class SPO, class GA, class CL>
+static void dirac_dispatch(const Geom &g, bool dag, SPI in, SPO out, GA U, CL C, double kappa, int nrhs,
                            cudaStream_t s)
 {
     const bool cube = g.lb[0] == g.lb[1] && g.lb[1] == g.lb[2] && g.lb[2] == g.lb[3];
@@ -267,6 +271,27 @@ int launch_dirac(const mgc_clover_s *op, int prec, bool dag, const void *in, voi
     MGC_CUDA(cudaGetLastError());
     count(1, (double)g.V * (2.0 * nrhs * spinor_site_bytes(prec) +
                             links_site_bytes(prec, prec == 64 ? 18 : ga->compress) + clover_site_bytes(prec)));
+    return MGC_OK;
+}
+
+// w = D z for an FP16 z (per-site scale) with the FP32 operator: FP32
+// arithmetic and result, the FP16 input read directly (the smoother's output
+// in the mixed-precision solve, with no FP32 copy of it)
+int launch_dirac_from16(const mgc_clover_s *op, const void *in16, void *out32, cudaStream_t s)
+{
+    const mgc_gauge_s *ga = op->gauge;
+    const Geom &g = ga->lat->g;
+    if (!has_prec(ga, 32)) return fail(MGC_ERR_INVALID_ARG, "no FP32 copy of the operator");
+    Clover32 C{(float4 *)op->C32, g.lvb};
+    if (ga->compress == 12)
+        dirac_dispatch(g, false, sp16(g, in16, 1), sp32(g, out32), Gauge32x12{(float4 *)ga->U32, g.lvb}, C,
+                       op->kappa, 1, s);
+    else
+        dirac_dispatch(g, false, sp16(g, in16, 1), sp32(g, out32), Gauge32x18{(float2 *)ga->U32, g.lvb}, C,
+                       op->kappa, 1, s);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * (spinor_site_bytes(16) + spinor_site_bytes(32) + links_site_bytes(32, ga->compress) +
+                            clover_site_bytes(32)));
     return MGC_OK;
 }
 

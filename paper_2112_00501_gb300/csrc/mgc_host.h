@@ -99,6 +99,8 @@ int launch_convert(const Geom &g, int nrhs, int pin, const void *in, int pout, v
 int launch_gauge_pack(const Geom &g, const double *canon_dev, int prec, int compress, void *out, cudaStream_t s);
 int launch_dirac(const mgc_clover_s *op, int prec, bool dag, const void *in, void *out, int nrhs,
                  cudaStream_t s);
+// w = D z with the FP32 operator for an FP16 z (FP32 result)
+int launch_dirac_from16(const mgc_clover_s *op, const void *in16, void *out32, cudaStream_t s);
 int launch_clover_apply(const mgc_clover_s *op, int prec, bool inverse, const void *in, void *out, int nrhs,
                         cudaStream_t s);
 int launch_gamma5(const Geom &g, int nrhs, const double2 *in, double2 *out, cudaStream_t s);

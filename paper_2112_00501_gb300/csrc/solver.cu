@@ -38,6 +38,7 @@ struct SolverWork {
     void *rl = nullptr, *zl = nullptr;
     float2 *r32 = nullptr;                  // two-level solve: FP32 inner vectors
     float2 *w32[MAXM] = {}, *z32[MAXM] = {};
+    void *z16[MAXM] = {};                   // FP16 smoother outputs (FP16 smoother)
     int m32 = 0;
     double *scal = nullptr;     // device scalars
     double *partial = nullptr;  // reduction partials
@@ -217,6 +218,7 @@ void free_work(mgc_clover_s *op)
     cudaFree(W->r32);
     for (auto p : W->w32) cudaFree(p);
     for (auto p : W->z32) cudaFree(p);
+    for (auto p : W->z16) cudaFree(p);
     cudaFree(W->scal);
     cudaFree(W->partial);
     cudaFree(W->counter);
@@ -264,6 +266,7 @@ static int ensure_work(mgc_clover_s *op, int method, int m, int lowprec)
         W->lowprec = 16;
         MGC_CUDA(cudaMalloc(&W->rl, spinor_bytes(g, 16, 1)));
         MGC_CUDA(cudaMalloc(&W->zl, spinor_bytes(g, 16, 1)));
+        for (int j = 0; j < W->m32; ++j) MGC_CUDA(cudaMalloc(&W->z16[j], spinor_bytes(g, 16, 1)));
     } else if (lowprec == 32 || keeplow == 32) {
         W->lowprec = 32;
         MGC_CUDA(cudaMalloc(&W->rl, spinor_bytes(g, 32, 1)));
@@ -855,13 +858,73 @@ static int precondition32(mgc_clover_s *op, const mgc_solve_params *p, const flo
 
 typedef std::complex<double> zd;
 
+// an FP16 packed spinor of one right-hand side: data, then one scale per site
+static Spinor16 view16(const Geom &g, void *p)
+{
+    uint4 *d = (uint4 *)p;
+    return Spinor16{d, (float *)(d + (size_t)g.V * 3), g.lvb};
+}
+
+// the FP16-smoother path of the inner FGCR: the smoother's FP16 output z_j is
+// kept as it is (no FP32 copy), the FP32 operator reads it directly, and the
+// residual update also writes the FP16 residual the smoother reads
+static bool fp16_directions(const mgc_solve_params *p) { return p->precond != 0 && p->smoother_prec == 16; }
+
+// One pass over sites for the FP16-smoother path: w'_j = w_j - sum_i c_i w'_i
+// and r -= alpha w'_j on the FP32 vectors, the FP16 copy of the new r, and
+// ||w'_j||^2, ||r||^2 into two device scalars from slot on
+static int orth_update_sites(mgc_clover_s *op, float2 *wj, const PtrList4 &Lw, const CoefList &C, int j, float2 alpha,
+                             float2 *r, void *rl, int slot, cudaStream_t s)
+{
+    SolverWork *W = op->work;
+    const Geom g = op->gauge->lat->g;
+    const int lvb = g.lvb;
+    const Spinor32 Wj{(float4 *)wj, lvb}, R{(float4 *)r, lvb};
+    const Spinor16 RL = view16(g, rl);
+    auto f = [=] __device__(long long i, double *acc) {
+        Cx<float> v[12];
+        Wj.load((int)i, v);
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+            if (q < j) {
+                const Spinor32 Wq{const_cast<float4 *>(Lw.p[q]), lvb};
+                Cx<float> u[12];
+                Wq.load((int)i, u);
+                const Cx<float> c = {C.c[q].x, C.c[q].y};
+#pragma unroll
+                for (int k = 0; k < 12; ++k) v[k] = v[k] - c * u[k];
+            }
+        Wj.store((int)i, v);
+        Cx<float> rv[12];
+        R.load((int)i, rv);
+        const Cx<float> a = {alpha.x, alpha.y};
+        float nw = 0.f, nr = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            nw += norm2(v[k]);
+            rv[k] = rv[k] - a * v[k];
+            nr += norm2(rv[k]);
+        }
+        R.store((int)i, rv);
+        RL.store((int)i, rv);
+        acc[0] += nw;
+        acc[1] += nr;
+    };
+    k_reduce<2><<<red_grid(g.V), RT, 0, s>>>((long long)g.V, f, W->partial, W->counter, W->scal + slot);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * (96.0 * (j + 4) + 52.0));
+    return MGC_OK;
+}
+
 // inner FGCR on W->r32 (unit norm on entry, residual on exit); fills gamma for
 // the k directions it built; *rr_out = final ||r||^2
 static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_in, double rr0, int max_it,
                         int *k_out, std::vector<zd> &gamma, double *rr_out, cudaStream_t s)
 {
     SolverWork *W = op->work;
-    const long long n = (long long)op->gauge->lat->g.V * 12;
+    const Geom &gm = op->gauge->lat->g;
+    const long long n = (long long)gm.V * 12;
+    const bool h16 = fp16_directions(p);  // W->rl holds the FP16 copy of r on entry
     const int m = p->restart < max_it ? p->restart : max_it;
     float2 *r = W->r32;
     double *sc = W->scal;
@@ -872,8 +935,14 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
     int k = 0;
     for (int j = 0; j < m; ++j) {
         float2 *zj = W->z32[j], *wj = W->w32[j];
-        MGC_TRY(precondition32(op, p, r, zj, s));
-        MGC_TRY(launch_dirac(op, 32, false, zj, wj, 1, s));
+        if (h16) {
+            MGC_CUDA(cudaMemsetAsync(W->z16[j], 0, spinor_bytes(gm, 16, 1), s));
+            MGC_TRY(run_sap(op, p, 16, W->rl, W->z16[j], s));
+            MGC_TRY(launch_dirac_from16(op, W->z16[j], wj, s));
+        } else {
+            MGC_TRY(precondition32(op, p, r, zj, s));
+            MGC_TRY(launch_dirac(op, 32, false, zj, wj, 1, s));
+        }
         // d_i = <w'_i, w_j> (i < j) and rho = <w_j, r>, eight at a time, and
         // ||w_j||^2 with the first eight
         std::vector<zd> d(j + 1);
@@ -927,7 +996,10 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
             // ||r||^2 come back from the same pass
             alpha[j] = rho / nw_est;
             const float2 a = make_float2((float)alpha[j].real(), (float)alpha[j].imag());
-            MGC_TRY(reduce32<2>(
+            if (h16) {
+                MGC_TRY(orth_update_sites(op, wj, Lw, C, j, a, r, W->rl, S_BETA, s));
+            } else {
+                MGC_TRY(reduce32<2>(
                 n,
                 [=] __device__(long long e, float *acc) {
                     float4 v = wj4[e];
@@ -944,6 +1016,7 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
                     facc_n2(acc + 1, hi2(u));
                 },
                 W, sc + S_BETA, s, 8.0 * n * (j + 4)));
+            }
             double h2[2];
             MGC_TRY(read_scalars(W, S_BETA, 2, h2, s));
             if (bad(h2[0]) || h2[0] == 0.0) return fail(MGC_ERR_BREAKDOWN, "inner FGCR: zero or non-finite direction");
@@ -983,6 +1056,7 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
                 facc_n2(acc, hi2(v));
             },
             W, sc + S_RR, s, 8.0 * n * 3));
+        if (h16) MGC_TRY(launch_convert(gm, 1, 32, r, 16, W->rl, s));
         MGC_TRY(read_scalars(W, S_RR, 1, &rr, s));
         k = j + 1;
         if (bad(rr)) return fail(MGC_ERR_BREAKDOWN, "inner FGCR: non-finite residual");
@@ -1000,17 +1074,20 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
 }
 
 // r32 = b - t site by site (the FP64 and FP32 packed layouts differ; t may be
-// null: r32 = b), and ||b - t||^2 into a device scalar slot.  The FP64
+// null: r32 = b), its FP16 copy into rl when rl is given (the FP16 smoother's
+// input), and ||b - t||^2 into a device scalar slot.  The FP64
 // residual itself is not kept: the inner solve only needs its FP32 copy, and
 // r32 is not normalised, since FP32 covers every residual this solve reaches
 // (down to tol ||b||).
-static int residual_to32(mgc_clover_s *op, const double2 *b, const double2 *t, float2 *r32, int slot, cudaStream_t s)
+static int residual_to32(mgc_clover_s *op, const double2 *b, const double2 *t, float2 *r32, void *rl, int slot,
+                         cudaStream_t s)
 {
     SolverWork *W = op->work;
     const Geom g = op->gauge->lat->g;
     const Spinor64 B{const_cast<double2 *>(b), g.lvb}, T{const_cast<double2 *>(t), g.lvb};
     const Spinor32 R{reinterpret_cast<float4 *>(r32), g.lvb};
-    const bool has_t = t != nullptr;
+    const bool has_t = t != nullptr, has_l = rl != nullptr;
+    const Spinor16 RL = has_l ? view16(g, rl) : Spinor16{nullptr, nullptr, g.lvb};
     auto f = [=] __device__(long long i, double *acc) {
         Cx<double> v[12];
         Cx<float> w[12];
@@ -1027,10 +1104,11 @@ static int residual_to32(mgc_clover_s *op, const double2 *b, const double2 *t, f
             acc[0] = fma(v[k].r, v[k].r, fma(v[k].i, v[k].i, acc[0]));
         }
         R.store((int)i, w);
+        if (has_l) RL.store((int)i, w);
     };
     k_reduce<1><<<red_grid(g.V), RT, 0, s>>>((long long)g.V, f, W->partial, W->counter, W->scal + slot);
     MGC_CUDA(cudaGetLastError());
-    count(1, (double)g.V * ((has_t ? 2 : 1) * 192.0 + 96.0));
+    count(1, (double)g.V * ((has_t ? 2 : 1) * 192.0 + 96.0 + (has_l ? 52.0 : 0.0)));
     return MGC_OK;
 }
 
@@ -1067,12 +1145,46 @@ static int axpy_sum32(mgc_clover_s *op, double2 *x, const PtrList4 &Lz, const Co
     return MGC_OK;
 }
 
+// x += sum_j gamma_j z_j for FP16 z_j (the FP16-smoother path), as axpy_sum32
+struct Spinor16List {
+    Spinor16 z[MAXM];
+};
+static int axpy_sum16(mgc_clover_s *op, double2 *x, const Spinor16List &Z, const CoefList &G, int k, cudaStream_t s)
+{
+    const Geom g = op->gauge->lat->g;
+    const Spinor64 X{x, g.lvb};
+    auto f = [=] __device__(long long i) {
+        Cx<float> e[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) e[c] = Cx<float>{0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+            if (j < k) {
+                Cx<float> z[12];
+                Z.z[j].load((int)i, z);
+                const Cx<float> gj = {G.c[j].x, G.c[j].y};
+#pragma unroll
+                for (int c = 0; c < 12; ++c) e[c] = cfma(gj, z[c], e[c]);
+            }
+        Cx<double> v[12];
+        X.load((int)i, v);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) v[c] = v[c] + Cx<double>{(double)e[c].r, (double)e[c].i};
+        X.store((int)i, v);
+    };
+    k_map<<<red_grid(g.V), RT, 0, s>>>((long long)g.V, f);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)g.V * (2 * 192.0 + 52.0 * k));
+    return MGC_OK;
+}
+
 static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
 {
     SolverWork *W = op->work;
     const long long n = (long long)op->gauge->lat->g.V * 12;
     double2 *x = W->x, *b = W->b, *t = W->t;
     float2 *r32 = W->r32;
+    void *rl = fp16_directions(p) ? W->rl : nullptr;  // the FP16 smoother's input
     double *sc = W->scal;
     double bb, rr;
     info->iters = 0;
@@ -1086,12 +1198,12 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
             return MGC_OK;
         }
         MGC_TRY(apply_D64(op, x, t, s));
-        MGC_TRY(residual_to32(op, b, t, r32, S_RR, s));
+        MGC_TRY(residual_to32(op, b, t, r32, rl, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
     } else {
         // x = 0: r = b, and ||b||^2 from the same pass
         MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
-        MGC_TRY(residual_to32(op, b, nullptr, r32, S_RR, s));
+        MGC_TRY(residual_to32(op, b, nullptr, r32, rl, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
         bb = rr;
         if (bb == 0.0) return MGC_OK;
@@ -1113,15 +1225,19 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
         MGC_TRY(inner_fgcr32(op, p, tin, rr, p->max_iter - iters, &k, gamma, &rri, s));
         iters += k;
         // x += e, e = sum_j gamma_j z_j
-        PtrList4 Lz{};
         CoefList G{};
-        for (int j = 0; j < k; ++j) {
-            Lz.p[j] = (const float4 *)W->z32[j];
-            G.c[j] = make_float2((float)gamma[j].real(), (float)gamma[j].imag());
+        for (int j = 0; j < k; ++j) G.c[j] = make_float2((float)gamma[j].real(), (float)gamma[j].imag());
+        if (rl) {
+            Spinor16List Z{};
+            for (int j = 0; j < k; ++j) Z.z[j] = view16(op->gauge->lat->g, W->z16[j]);
+            MGC_TRY(axpy_sum16(op, x, Z, G, k, s));
+        } else {
+            PtrList4 Lz{};
+            for (int j = 0; j < k; ++j) Lz.p[j] = (const float4 *)W->z32[j];
+            MGC_TRY(axpy_sum32(op, x, Lz, G, k, s));
         }
-        MGC_TRY(axpy_sum32(op, x, Lz, G, k, s));
         MGC_TRY(apply_D64(op, x, t, s));
-        MGC_TRY(residual_to32(op, b, t, r32, S_RR, s));
+        MGC_TRY(residual_to32(op, b, t, r32, rl, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
         info->iters = iters;
         info->restarts++;
