@@ -1055,6 +1055,282 @@ static int sap_run_h16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clo
     return MGC_OK;
 }
 
+// ------------------------------------------------------------------ FP32-storage kernel
+// FP32 fields on 2^4 and 4^4 domains with the domain size known at compile
+// time.  Shared memory holds the domain's links as 18-real FP32 (a 12-real
+// copy is brought in by TMA into the upper two thirds of that area and
+// expanded once) and r as pairs of complex numbers; e stays in registers and
+// the clover term is read from global memory at each use (it stays in L2
+// across the MR steps).  About 98 KB of shared memory: two blocks per SM,
+// where keeping the clover term in shared memory as well allows one.
+
+template <class GA> struct F32Links;
+template <> struct F32Links<Gauge32x12> {
+    static constexpr bool EXPAND = true;
+    static constexpr int STAGE = 192;  // bytes per site of the staged copy
+    static __device__ const void *src(const Gauge32x12 &U, int blk, int lvb) { return U.p + ((size_t)blk * 12 << lvb); }
+};
+template <> struct F32Links<Gauge32x18> {
+    static constexpr bool EXPAND = false;
+    static constexpr int STAGE = 288;
+    static __device__ const void *src(const Gauge32x18 &U, int blk, int lvb) { return U.p + ((size_t)blk * 36 << lvb); }
+};
+
+template <int LVB>
+__host__ __device__ constexpr size_t f32_smem_bytes()
+{
+    return (size_t)(1 << LVB) * (288 + 96) + 96 * 4 + 16;
+}
+
+template <int MU, int SGN, int VB>
+__device__ __forceinline__ void f32_hop(const float4 *rs, int n, const float2 *sL, int lk, Cx<float> acc[12])
+{
+    Cx<float> s[12], h[6], w[6], u[9];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float4 v = rs[k * VB + n];
+        s[2 * k] = {v.x, v.y};
+        s[2 * k + 1] = {v.z, v.w};
+    }
+    project<MU, SGN>(s, h);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float2 v = sL[(MU * 9 + k) * VB + lk];
+        u[k] = {v.x, v.y};
+    }
+    if (SGN < 0) su3_mul(u, h, w);
+    else su3_dag_mul(u, h, w);
+    reconstruct_add<MU, SGN>(acc, w);
+}
+
+template <int VB>
+__device__ __forceinline__ void f32_hops(const float4 *rs, const float2 *sL, int l, const int nf[4], const int nb[4],
+                                         Cx<float> acc[12])
+{
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = Cx<float>{0.f, 0.f};
+    if (nf[0] >= 0) f32_hop<0, -1, VB>(rs, nf[0], sL, l, acc);
+    if (nb[0] >= 0) f32_hop<0, +1, VB>(rs, nb[0], sL, nb[0], acc);
+    if (nf[1] >= 0) f32_hop<1, -1, VB>(rs, nf[1], sL, l, acc);
+    if (nb[1] >= 0) f32_hop<1, +1, VB>(rs, nb[1], sL, nb[1], acc);
+    if (nf[2] >= 0) f32_hop<2, -1, VB>(rs, nf[2], sL, l, acc);
+    if (nb[2] >= 0) f32_hop<2, +1, VB>(rs, nb[2], sL, nb[2], acc);
+    if (nf[3] >= 0) f32_hop<3, -1, VB>(rs, nf[3], sL, l, acc);
+    if (nb[3] >= 0) f32_hop<3, +1, VB>(rs, nb[3], sL, nb[3], acc);
+}
+
+// one domain solve of the FP32 kernel: domain jb of `colour`, right-hand side
+// rr; C is the clover term (MR on D_B) or its inverse (Jacobi on A_B)
+template <bool JAC, int LVB, class GA>
+__device__ __forceinline__ void sap_f32_body(const Geom &g, const Spinor32 &b, const Spinor32 &x, const GA &U,
+                                             const Clover32 &C, float kappa, int colour, int nmr, int x_zero,
+                                             int *status, int jb, int rr)
+{
+    constexpr int VB = 1 << LVB;
+    constexpr int LB = LVB / 4;
+    using FL = F32Links<GA>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2 *sL = reinterpret_cast<float2 *>(smem);           // [4][9][VB]
+    float4 *rs = reinterpret_cast<float4 *>(sL + 36 * VB);   // [6][VB]
+    float *red = reinterpret_cast<float *>(rs + 6 * VB);     // 96 floats
+    uint64_t *bar = reinterpret_cast<uint64_t *>(red + 96);
+    // the 12-real copy lands in the upper 192 B per site of the link area
+    float4 *stage = reinterpret_cast<float4 *>(sL + 12 * VB);
+
+    Geom gg = g;
+    gg.lvb = LVB;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) gg.lb[mu] = LB;
+    Spinor32 bb = shift_rhs(b, rr, g.V), xx = shift_rhs(x, rr, g.V);
+    bb.lvb = LVB;
+    xx.lvb = LVB;
+    GA Ug = U;
+    Ug.lvb = LVB;
+    Clover32 Cg = C;
+    Cg.lvb = LVB;
+    int j = jb;
+    const int half0 = g.NB[0] >> 1;
+    int bc[4];
+    const int m = j % half0;
+    j /= half0;
+    bc[1] = j % g.NB[1];
+    j /= g.NB[1];
+    bc[2] = j % g.NB[2];
+    bc[3] = j / g.NB[2];
+    bc[0] = 2 * m + ((colour + bc[1] + bc[2] + bc[3]) & 1);
+    const int blk = block_index(gg, bc);
+    const int l = threadIdx.x;
+    const int i = (blk << LVB) | l;
+
+    if (l == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (l == 0) {
+        const unsigned lbytes = FL::STAGE * VB;
+        mbar_arrive_expect_tx(bar, lbytes);
+        bulk_g2s(FL::EXPAND ? (void *)stage : (void *)sL, FL::src(U, blk, LVB), lbytes, bar);
+    }
+
+    int lc[4], cg[4];
+    local_coords(gg, l, lc);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) cg[mu] = (bc[mu] << LB) + lc[mu];
+
+    // 1. hopping part of D x from global memory while the copy lands
+    Cx<float> acc[12];
+    if (!x_zero) hop_site<false>(gg, cg, i, xx, Ug, acc);
+
+    const bool ok = mbar_wait_bounded(bar, 0, WAIT_LIMIT_NS);
+    if (!__syncthreads_and(ok)) {
+        mbar_wait_bounded(bar, 0, WAIT_LIMIT_NS);
+        if (l == 0) atomicOr(status, MGC_DEV_TIMEOUT);
+        return;
+    }
+    if (FL::EXPAND) {
+        // rows 0 and 1 of this site's four links, then row 2 = conj(row0 x row1)
+        // written over the staged copy once every thread has read its own
+        float4 st[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) st[k] = stage[k * VB + l];
+        __syncthreads();
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            Cx<float> u[9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float4 v = st[mu * 3 + k];
+                u[2 * k] = {v.x, v.y};
+                u[2 * k + 1] = {v.z, v.w};
+            }
+            reconstruct_row2(u);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sL[(mu * 9 + k) * VB + l] = make_float2(u[k].r, u[k].i);
+        }
+    }
+
+    // r_B = b - D x on the domain (MR), or the residual of A = C^-1 D (Jacobi)
+    Cx<float> rv[12];
+    bb.load(i, rv);
+    if (!x_zero) {
+        Cx<float> xs[12], cx[12];
+        xx.load(i, xs);
+        if (JAC) {
+            clover_site(Cg, i, acc, cx);  // C^-1 H x
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                rv[k] = Cx<float>{fmaf(kappa, cx[k].r, rv[k].r - xs[k].r), fmaf(kappa, cx[k].i, rv[k].i - xs[k].i)};
+        } else {
+            clover_site(Cg, i, xs, cx);
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                rv[k] = Cx<float>{rv[k].r - fmaf(-kappa, acc[k].r, cx[k].r),
+                                  rv[k].i - fmaf(-kappa, acc[k].i, cx[k].i)};
+        }
+    }
+    int nf[4], nb[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        int t[4] = {lc[0], lc[1], lc[2], lc[3]};
+        t[mu] = lc[mu] + 1;
+        nf[mu] = (t[mu] < (1 << LB)) ? local_index(gg, t) : -1;
+        t[mu] = lc[mu] - 1;
+        nb[mu] = (t[mu] >= 0) ? local_index(gg, t) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) rs[k * VB + l] = make_float4(rv[2 * k].r, rv[2 * k].i, rv[2 * k + 1].r, rv[2 * k + 1].i);
+    Cx<float> e[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) e[k] = Cx<float>{0.f, 0.f};
+    __syncthreads();
+
+    // 2'. Jacobi on A_B with e in shared memory (rs): e_1 = r_B, then
+    // e <- r_B + kappa C^-1 H_B e
+    if (JAC) {
+        if (nmr >= 1)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) e[k] = rv[k];
+        for (int it = 1; it < nmr; ++it) {
+            f32_hops<VB>(rs, sL, l, nf, nb, acc);
+            Cx<float> t[12];
+            clover_site(Cg, i, acc, t);
+            __syncthreads();  // every thread has read e before it is replaced
+#pragma unroll
+            for (int k = 0; k < 12; ++k) e[k] = Cx<float>{fmaf(kappa, t[k].r, rv[k].r), fmaf(kappa, t[k].i, rv[k].i)};
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                rs[k * VB + l] = make_float4(e[2 * k].r, e[2 * k].i, e[2 * k + 1].r, e[2 * k + 1].i);
+            __syncthreads();
+        }
+        nmr = 0;
+    }
+
+    // 2. minimal residual on D_B
+    for (int it = 0; it < nmr; ++it) {
+        f32_hops<VB>(rs, sL, l, nf, nb, acc);
+        Cx<float> rv2[12], p[12];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 v = rs[k * VB + l];
+            rv2[2 * k] = {v.x, v.y};
+            rv2[2 * k + 1] = {v.z, v.w};
+        }
+        clover_site(Cg, i, rv2, p);
+        float pr = 0.f, pi = 0.f, pp = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            p[k] = Cx<float>{fmaf(-kappa, acc[k].r, p[k].r), fmaf(-kappa, acc[k].i, p[k].i)};
+            pr = fmaf(p[k].r, rv2[k].r, fmaf(p[k].i, rv2[k].i, pr));
+            pi = fmaf(p[k].r, rv2[k].i, fmaf(-p[k].i, rv2[k].r, pi));
+            pp = fmaf(p[k].r, p[k].r, fmaf(p[k].i, p[k].i, pp));
+        }
+        block_sum3(pr, pi, pp, red);
+        const Cx<float> alpha = (pp > 0.f) ? Cx<float>{pr / pp, pi / pp} : Cx<float>{0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            e[k] = cfma(alpha, rv2[k], e[k]);
+            rv2[k] = rv2[k] - alpha * p[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            rs[k * VB + l] = make_float4(rv2[2 * k].r, rv2[2 * k].i, rv2[2 * k + 1].r, rv2[2 * k + 1].i);
+        __syncthreads();
+    }
+
+    // 3. x_B += e
+    if (!x_zero) {
+        Cx<float> xo[12];
+        xx.load(i, xo);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) e[k] = e[k] + xo[k];
+    }
+    xx.store(i, e);
+}
+
+template <bool JAC, int LVB, class GA>
+__global__ void __launch_bounds__(1 << LVB, 2) k_sap_f32(Geom g, Spinor32 b, Spinor32 x, GA U, Clover32 C, float kappa,
+                                                         int colour, int nmr, int x_zero, int *status)
+{
+    sap_f32_body<JAC, LVB>(g, b, x, U, C, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
+}
+
+template <bool JAC, int LVB, class GA>
+static int sap_run_f32(const mgc_clover_s *op, Spinor32 b, Spinor32 x, GA U, Clover32 C, int nrhs, int n_cy, int n_mr,
+                       int x_is_zero, cudaStream_t s, int compress)
+{
+    const Geom &g = op->gauge->lat->g;
+    constexpr size_t smem = f32_smem_bytes<LVB>();
+    auto kern = k_sap_f32<JAC, LVB, GA>;
+    MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(g.nblocks / 2, nrhs);
+    for (int cy = 0; cy < n_cy; ++cy)
+        for (int colour = 0; colour < 2; ++colour) {
+            const int xz = (cy == 0 && colour == 0) ? x_is_zero : 0;
+            kern<<<grid, 1 << LVB, smem, s>>>(g, b, x, U, C, (float)op->kappa, colour, n_mr, xz, op->d_status);
+            count(1, sap_launch_bytes(g, 32, compress, nrhs, xz != 0));
+        }
+    MGC_CUDA(cudaGetLastError());
+    return MGC_OK;
+}
+
 // FP16 storage: the compile-time kernel for cubic 2^4 and 4^4 domains
 template <int MODE, class SP, class GA, class CL>
 static int sap_run_staged(const mgc_clover_s *op, SP b, SP x, GA U, CL C, CL Ci, int nrhs, int n_cy, int n_mr,
@@ -1113,6 +1389,15 @@ __global__ void __launch_bounds__(1 << LVB, 2) k_sap_h16_batch(SapBatch<Spinor16
     int k, jb, rr;
     batch_item(B, k, jb, rr);
     sap_h16_body<false, LVB>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
+}
+
+template <int LVB, class GA>
+__global__ void __launch_bounds__(1 << LVB, 2) k_sap_f32_batch(SapBatch<Spinor32, GA, Clover32> B, int colour, int nmr,
+                                                               int x_zero)
+{
+    int k, jb, rr;
+    batch_item(B, k, jb, rr);
+    sap_f32_body<false, LVB>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
 }
 
 // one block per SM: selecting the lattice at run time costs registers that a
@@ -1219,6 +1504,8 @@ int launch_sap_batch(const BatchSpec &spec, int prec, const void *const *b, void
             B.U[k] = Gauge32x12{(float4 *)op->gauge->U32, g.lvb};
             B.C[k] = Clover32{(float4 *)op->C32, g.lvb};
         }
+        if (cube && g0.lvb == 8) return run(k_sap_f32_batch<8, Gauge32x12>, B, f32_smem_bytes<8>());
+        if (cube && g0.lvb == 4) return run(k_sap_f32_batch<4, Gauge32x12>, B, f32_smem_bytes<4>());
         return run(k_sap_staged_batch<Spinor32, Gauge32x12, Clover32>, B, staged_smem<Gauge32x12, Clover32>(vb));
     }
     SapBatch<Spinor32, Gauge32x18, Clover32> B;
@@ -1231,6 +1518,8 @@ int launch_sap_batch(const BatchSpec &spec, int prec, const void *const *b, void
         B.U[k] = Gauge32x18{(float2 *)op->gauge->U32, g.lvb};
         B.C[k] = Clover32{(float4 *)op->C32, g.lvb};
     }
+    if (cube && g0.lvb == 8) return run(k_sap_f32_batch<8, Gauge32x18>, B, f32_smem_bytes<8>());
+    if (cube && g0.lvb == 4) return run(k_sap_f32_batch<4, Gauge32x18>, B, f32_smem_bytes<4>());
     return run(k_sap_staged_batch<Spinor32, Gauge32x18, Clover32>, B, staged_smem<Gauge32x18, Clover32>(vb));
 }
 
@@ -1325,6 +1614,16 @@ static int sap_launch_impl(const mgc_clover_s *op, int prec, const void *b, void
     if (prec == 32) {
         Spinor32 B{(float4 *)b, g.lvb}, X{(float4 *)x, g.lvb};
         Clover32 C{(float4 *)(jac ? op->Ci32 : op->C32), g.lvb}, Ci{(float4 *)op->Ci32, g.lvb};
+        const bool cube = g.lb[0] == g.lb[1] && g.lb[1] == g.lb[2] && g.lb[2] == g.lb[3];
+        if (MODE != SAP_EO && cube && (g.lvb == 8 || g.lvb == 4)) {
+            const Gauge32x12 U12{(float4 *)ga->U32, g.lvb};
+            const Gauge32x18 U18{(float2 *)ga->U32, g.lvb};
+            if (g.lvb == 8)
+                return cp == 12 ? sap_run_f32<jac, 8>(op, B, X, U12, C, nrhs, n_cy, n_it, x_is_zero, s, cp)
+                                : sap_run_f32<jac, 8>(op, B, X, U18, C, nrhs, n_cy, n_it, x_is_zero, s, cp);
+            return cp == 12 ? sap_run_f32<jac, 4>(op, B, X, U12, C, nrhs, n_cy, n_it, x_is_zero, s, cp)
+                            : sap_run_f32<jac, 4>(op, B, X, U18, C, nrhs, n_cy, n_it, x_is_zero, s, cp);
+        }
         if (cp == 12)
             return sap_run_staged<MODE>(op, B, X, Gauge32x12{(float4 *)ga->U32, g.lvb}, C, Ci, nrhs, n_cy, n_it,
                                         x_is_zero, s, prec, cp);
