@@ -31,9 +31,12 @@ namespace mgc {
 namespace {
 
 constexpr int BRT = 256;       // threads of the segmented kernels
-constexpr int BCHUNK = 4096;   // elements per segmented block
+// elements per segmented block: 64 per thread, so the block's FP64 reduction
+// of up to 16 accumulators is amortised over enough data (with 16 per thread
+// the Gram-Schmidt pass ran at a quarter of HBM bandwidth)
+constexpr int BCHUNK = 16384;
 constexpr int BMAXM = 16;      // longest inner cycle of the batched solve
-constexpr int BCH32 = 8;       // FP32 accumulation chunk
+constexpr int BCH32 = 16;      // FP32 accumulation chunk
 
 // per-system scalars of the batched solve
 struct SysScal {
