@@ -436,15 +436,15 @@ def profile_kernel(which):
                                       compress=w["compress"]), w["kappa"], w["csw"])
     bp = lat.pack(b, w["prec"])
     xp = lat.zeros_packed(w["prec"])
-    prec = {"dslash64": 64, "dslash32": 32}.get(which, w["prec"])
+    prec = {"dslash64": 64, "dslash32": 32, "sap32": 32}.get(which, w["prec"])
     if prec != w["prec"]:
         bp, xp = lat.pack(b, prec), lat.empty_packed(prec)
     if which == "dslash16x18":
         op = api.CloverOperator(api.Gauge(lat, torch.from_numpy(U).cuda(), storage_prec=w["prec"], compress=18),
                                 w["kappa"], w["csw"])
     for _ in range(2):
-        if which == "sap":
-            op.sap_smooth(bp, xp, w["prec"], 1, 1, w["n_mr"], x_is_zero=False)
+        if which in ("sap", "sap32"):
+            op.sap_smooth(bp, xp, prec, 1, 1, w["n_mr"], x_is_zero=False)
         else:
             op.apply_D(bp, prec, 1, xp)
     torch.cuda.synchronize()
@@ -465,7 +465,7 @@ def main():
     ap.add_argument("--no-force", action="store_true")
     ap.add_argument("--no-qws", action="store_true")
     ap.add_argument("--no-mg", action="store_true")
-    ap.add_argument("--profile-kernel", choices=["sap", "dslash", "dslash32", "dslash16x18", "dslash64"],
+    ap.add_argument("--profile-kernel", choices=["sap", "sap32", "dslash", "dslash32", "dslash16x18", "dslash64"],
                     default=None,
                     help="run only a few launches of one kernel on 24^3x48 (for ncu captures)")
     args = ap.parse_args()
