@@ -213,6 +213,9 @@ BATCH_WORKLOAD = dict(lattices=[((24, 24, 24, 48), 12), ((16, 16, 16, 16), 8), (
                       n_cy=4, n_mr=4, restart=16, tol=1e-10, inner_tol=2e-6)
 # two-level multigrid on the bench system: the paper's 8x4x4x4 aggregates and 16 null vectors
 MG_AGG, MG_NVEC, MG_RHS = (8, 4, 4, 4), 16, 12
+# the mid-size single-lattice case: FP32 fields and smoother inside FP64 FGCR
+C1_WORKLOAD = dict(dims=(16, 16, 16, 32), block=(4, 4, 4, 4), eps=0.4, kappa=0.1355, csw=1.0, config_index=1,
+                   prec=32, compress=18, n_cy=4, n_mr=4, restart=16, tol=1e-10, inner_tol=2e-6)
 # link force workload
 FORCE_WORKLOAD = dict(dims=(24, 24, 24, 48), block=(4, 4, 4, 4), eps=0.4, kappa=0.1355, csw=1.0, config_index=4,
                       prec=32, compress=18)
@@ -386,6 +389,58 @@ def bench_mg(lib, stream, op, b, params, w):
                                    "two_level_solves_s": t_tl12}}
 
 
+def bench_c1(lib, stream):
+    """16^3 x 32 with FP32 fields: D (FP32, FP64), one smoother sweep (FP32,
+    4 MR steps per domain, both colours) and the solve to 1e-10 with FP64
+    FGCR around the FP32 smoother, beside the default two-level solve.  The
+    fields (about 110 MB at FP32) fit in the 129 MB L2, so its GB/s figures
+    are L2-assisted, not HBM figures."""
+    import torch
+
+    from paper_2112_00501_gb300 import api, synth
+
+    cw = C1_WORKLOAD
+    dims = cw["dims"]
+    U = synth.gauge_field(dims, cw["eps"], synth.gauge_seed(cw["config_index"]))
+    b = torch.from_numpy(synth.gaussian_spinor(dims, synth.source_seed(cw["config_index"]))).cuda()
+    lat = api.Lattice(dims, cw["block"], -1)
+    op = api.CloverOperator(api.Gauge(lat, torch.from_numpy(U).cuda(), storage_prec=cw["prec"],
+                                      compress=cw["compress"]), cw["kappa"], cw["csw"])
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        counters(lib, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        _, nb = counters(lib, reset=True)
+        t = e0.elapsed_time(e1) / 1e3 / n
+        return t, nb / n, out
+
+    res = {"workload": f"{'x'.join(map(str, dims))}, eps={cw['eps']}, kappa={cw['kappa']}, c_sw={cw['csw']}, "
+                       f"FP32 storage (18-real links), SAP {cw['n_cy']} sweeps x {cw['n_mr']} MR on 4^4 domains",
+           "note": "fields fit in L2: GB/s are L2-assisted"}
+    for prec in (32, 64):
+        xin, out = lat.pack(b, prec), lat.empty_packed(prec)
+        t, nb, _ = timed(lambda: op.apply_D(xin, prec, 1, out), 20)
+        res[f"dslash_fp{prec}"] = {"us": 1e6 * t, "gbs": nb / t / 1e9}
+    rl, zl = lat.pack(b, 32), lat.zeros_packed(32)
+    t, nb, _ = timed(lambda: op.sap_smooth(rl, zl, 32, 1, 1, cw["n_mr"], x_is_zero=False), 10)
+    res["sap_sweep_fp32"] = {"us": 1e6 * t, "gbs": nb / t / 1e9}
+    for name, method in (("fgcr_fp64_outer", 0), ("two_level", 2)):
+        params = api.solve_params(method=method, precond=1, smoother_prec=32, n_cy=cw["n_cy"], n_mr=cw["n_mr"],
+                                  restart=cw["restart"], tol=cw["tol"], max_iter=500, inner_tol=cw["inner_tol"])
+        t, nb, (x, info) = timed(lambda: op.solve(b, params), 3)
+        if info.status != 0 or not info.true_res <= cw["tol"]:
+            raise RuntimeError(f"c1 {name} solve failed: status {info.status}, residual {info.true_res}")
+        res[name] = {"ms": 1e3 * t, "iters": info.iters, "true_res": info.true_res, "gbs": nb / t / 1e9}
+    return res
+
+
 def bench_force(lib, stream):
     """dS/dU for S = phi^+ (D^+ D)^-1 phi on 24^3 x 48 (two solves and the
     force kernels)."""
@@ -465,6 +520,7 @@ def main():
     ap.add_argument("--no-force", action="store_true")
     ap.add_argument("--no-qws", action="store_true")
     ap.add_argument("--no-mg", action="store_true")
+    ap.add_argument("--no-c1", action="store_true")
     ap.add_argument("--profile-kernel", choices=["sap", "sap32", "dslash", "dslash32", "dslash16x18", "dslash64"],
                     default=None,
                     help="run only a few launches of one kernel on 24^3x48 (for ncu captures)")
@@ -702,6 +758,7 @@ def main():
     mgres = None if args.no_mg else bench_mg(lib, stream, op, b, params, w)
     batch = None if args.no_batch else bench_batch(lib, stream)
     force = None if args.no_force else bench_force(lib, stream)
+    c1 = None if args.no_c1 else bench_c1(lib, stream)
     counters(lib, reset=True)
 
     # ---------------- reduce over ranks
@@ -770,6 +827,7 @@ def main():
         "multigrid": mgres,
         "batched": batch,
         "force": force,
+        "c1": c1,
     }
     if not args.no_cpu_baseline:
         dt, it, Vs, thr = oracle_solve_sample(CPU_SAMPLE_DIMS)
