@@ -660,11 +660,12 @@ int mg_solve(mgc_mg_s *M, const double *b, double *x, const mgc_solve_params *p,
 // ------------------------------------------------------------------ two-level solve
 // FP64 defect correction (the double-precision Richardson iteration around a
 // single-precision solver of Sec. 2) with an FP32 inner FGCR(m) preconditioned
-// by SAP:  r = b - D x in FP64;  solve D e = r / ||r|| to inner_tol with FP32
-// vectors and the FP32 operator;  x += ||r|| e in FP64;  repeat until the FP64
-// true residual meets tol.  Inner products of the FP32 vectors accumulate in
-// FP32 over chunks of 8 entries per thread and in FP64 beyond that; the
-// Gram-Schmidt coefficients and step lengths are FP64 host scalars.  The inner
+// by SAP:  r = b - D x in FP64;  solve D e = r to inner_tol ||r|| with FP32
+// vectors and the FP32 operator (r enters as its unnormalised FP32 copy);
+// x += e in FP64;  repeat until the FP64 true residual meets tol.  Inner
+// products of the FP32 vectors accumulate in FP32 over chunks of entries per
+// thread and in FP64 beyond that; the Gram-Schmidt coefficients and step
+// lengths are FP64 host scalars.  The inner
 // FGCR never rescales or orthogonalises the z vectors: with w'_j = w_j -
 // sum_i c_ij w'_i and alpha_j = <w'_j, r>/||w'_j||^2, the correction is
 // e = sum_j gamma_j z_j with R gamma = alpha, R unit upper triangular with
@@ -916,8 +917,10 @@ static int orth_update_sites(mgc_clover_s *op, float2 *wj, const PtrList4 &Lw, c
     return MGC_OK;
 }
 
-// inner FGCR on W->r32 (unit norm on entry, residual on exit); fills gamma for
-// the k directions it built; *rr_out = final ||r||^2
+// inner FGCR on W->r32 (||r||^2 = rr0 on entry, the residual on exit; with
+// the FP16 smoother W->rl holds the FP16 copy of r on entry and is kept
+// current); stops at ||r|| <= tol_in sqrt(rr0); fills gamma for the k
+// directions it built; *rr_out = final ||r||^2
 static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_in, double rr0, int max_it,
                         int *k_out, std::vector<zd> &gamma, double *rr_out, cudaStream_t s)
 {
