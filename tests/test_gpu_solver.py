@@ -82,6 +82,38 @@ def test_multiple_rhs_and_initial_guess():
     assert info2.status == 0 and info2.iters == 0
 
 
+@pytest.mark.parametrize("smoother,compress", [(32, 18), (16, 12)])
+def test_two_level_long_inner_solves(smoother, compress):
+    """A weak smoother (one sweep, one MR step) and a tight inner tolerance make
+    an inner FGCR pass build more than eight directions, so the Gram-Schmidt
+    inner products take several multi-dot passes; with the FP16 smoother the
+    directions stay in FP16.  The solve still reaches the oracle's 1e-10."""
+    name = "mid_8^4"
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    op = _op(name, smoother, compress)
+    x, info = op.solve(torch.from_numpy(psi).cuda(), method=2, smoother_prec=smoother, n_cy=1, n_mr=1,
+                       restart=16, inner_tol=1e-7, tol=1e-10, max_iter=400)
+    assert info.status == 0 and info.true_res <= 1e-10
+    assert info.iters > 8 * info.restarts  # some pass went beyond eight directions
+    assert _oracle_residual(name, x.cpu().numpy()) <= 1e-10
+
+
+def test_two_level_from_a_guess_fp16():
+    """From a perturbed guess the first FP32/FP16 residual copies come from
+    b - D x0; the solve then matches the oracle's solution."""
+    from paper_2112_00501_gb300 import synth
+
+    name = "mid_8^4"
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    op = _op(name, 16, 12)
+    x, info = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=16)
+    assert info.status == 0
+    x0 = x.cpu().numpy() + 1e-3 * synth.gaussian_spinor(dims, 701)
+    x2, info2 = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=16, x0=x0)
+    assert info2.status == 0 and 0 < info2.iters < info.iters
+    assert _oracle_residual(name, x2.cpu().numpy()) <= 1e-10
+
+
 def test_solver_failure_modes_reported():
     """Host-injected faults: a NaN source is a breakdown, a zero source gives
     x = 0, and too few iterations give NOT_CONVERGED with the residual filled."""
