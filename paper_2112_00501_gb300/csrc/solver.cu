@@ -702,13 +702,14 @@ __device__ __forceinline__ void finish_reduce(double *acc, double (*sh)[RT / 32]
 // FP32 vectors are read as float4 (two complex entries per load).  Each thread
 // takes U4 independent float4 entries per step (grid stride apart, so a warp's
 // loads stay contiguous) to keep enough loads in flight to cover HBM latency;
-// its FP32 partial sums go to FP64 every flush_steps<NV>() steps.  With many
-// sums (the Gram-Schmidt inner products) a flush per step made the kernel
-// FP64-bound on GB300 (NV conversions and additions per four entries), so
-// those flush every fourth step: an FP32 partial then holds 16 float4 entries.
+// its FP32 partial sums go to FP64 every flush_steps<NV>() steps.  With
+// several sums (the Gram-Schmidt inner products) a flush per step made the
+// kernel FP64-bound on GB300 (NV conversions and additions per four entries),
+// so those flush every fourth step: an FP32 partial then holds 16 float4
+// entries.
 constexpr int U4 = 4;
 template <int NV>
-__host__ __device__ constexpr int flush_steps() { return NV >= 8 ? 4 : 1; }
+__host__ __device__ constexpr int flush_steps() { return NV >= 2 ? 4 : 1; }
 
 template <int NV, class F>
 __global__ void __launch_bounds__(RT) k_reduce32(long long n4, F f, double *partial, unsigned *counter, double *out)
@@ -917,6 +918,31 @@ static int orth_update_sites(mgc_clover_s *op, float2 *wj, const PtrList4 &Lw, c
     return MGC_OK;
 }
 
+// <L_q, v> for the CNT vectors of L (2 CNT sums) and, when norm is set,
+// ||v||^2 (one more), into 2 CNT + 1 device scalars from out on; one
+// instantiation per count, so only the sums in use are carried to FP64
+template <int CNT>
+static int multidot(long long n, const PtrList4 &L, const float4 *v, bool norm, SolverWork *W, double *out,
+                    cudaStream_t s)
+{
+    return reduce32<2 * CNT + 1>(
+        n,
+        [=] __device__(long long e, float *acc) {
+            const float4 x = v[e];
+#pragma unroll
+            for (int q = 0; q < CNT; ++q) {
+                const float4 a = L.p[q][e];
+                facc_dot(acc + 2 * q, lo2(a), lo2(x));
+                facc_dot(acc + 2 * q, hi2(a), hi2(x));
+            }
+            if (norm) {
+                facc_n2(acc + 2 * CNT, lo2(x));
+                facc_n2(acc + 2 * CNT, hi2(x));
+            }
+        },
+        W, out, s, 8.0 * n * (CNT + 1));
+}
+
 // inner FGCR on W->r32 (||r||^2 = rr0 on entry, the residual on exit; with
 // the FP16 smoother W->rl holds the FP16 copy of r on entry and is kept
 // current); stops at ||r|| <= tol_in sqrt(rr0); fills gamma for the k
@@ -956,28 +982,20 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
             // <L_q, w_j> with L = (w'_0 .. w'_{j-1}, r)
             PtrList4 L{};
             for (int q = 0; q < cnt; ++q) L.p[q] = (const float4 *)((i0 + q < j) ? W->w32[i0 + q] : r);
-            const float4 *wv = (const float4 *)wj;
-            MGC_TRY(reduce32<17>(
-                n,
-                [=] __device__(long long e, float *acc) {
-                    const float4 v = wv[e];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (q < cnt) {
-                            const float4 a = L.p[q][e];
-                            facc_dot(acc + 2 * q, lo2(a), lo2(v));
-                            facc_dot(acc + 2 * q, hi2(a), hi2(v));
-                        }
-                    if (first) {
-                        facc_n2(acc + 16, lo2(v));
-                        facc_n2(acc + 16, hi2(v));
-                    }
-                },
-                W, sc + S_BETA, s, 8.0 * n * (cnt + 1)));
+            switch (cnt) {
+                case 1: MGC_TRY(multidot<1>(n, L, (const float4 *)wj, first, W, sc + S_BETA, s)); break;
+                case 2: MGC_TRY(multidot<2>(n, L, (const float4 *)wj, first, W, sc + S_BETA, s)); break;
+                case 3: MGC_TRY(multidot<3>(n, L, (const float4 *)wj, first, W, sc + S_BETA, s)); break;
+                case 4: MGC_TRY(multidot<4>(n, L, (const float4 *)wj, first, W, sc + S_BETA, s)); break;
+                case 5: MGC_TRY(multidot<5>(n, L, (const float4 *)wj, first, W, sc + S_BETA, s)); break;
+                case 6: MGC_TRY(multidot<6>(n, L, (const float4 *)wj, first, W, sc + S_BETA, s)); break;
+                case 7: MGC_TRY(multidot<7>(n, L, (const float4 *)wj, first, W, sc + S_BETA, s)); break;
+                default: MGC_TRY(multidot<8>(n, L, (const float4 *)wj, first, W, sc + S_BETA, s)); break;
+            }
             double h[17];
-            MGC_TRY(read_scalars(W, S_BETA, first ? 17 : 2 * cnt, h, s));
+            MGC_TRY(read_scalars(W, S_BETA, 2 * cnt + 1, h, s));
             for (int q = 0; q < cnt; ++q) d[i0 + q] = zd(h[2 * q], h[2 * q + 1]);
-            if (first) ww = h[16];
+            if (first) ww = h[2 * cnt];
         }
         const zd rho = std::conj(d[j]);  // <w_j, r>
         // w'_j = w_j - sum_i c_i w'_i, c_i = d_i / ||w'_i||^2
