@@ -37,6 +37,7 @@ constexpr int BRT = 256;       // threads of the segmented kernels
 constexpr int BCHUNK = 16384;
 constexpr int BMAXM = 16;      // longest inner cycle of the batched solve
 constexpr int BCH32 = 16;      // FP32 accumulation chunk
+constexpr int SU = 4;          // elements per thread per step of the segmented kernels
 
 // per-system scalars of the batched solve
 struct SysScal {
@@ -113,10 +114,15 @@ __global__ void __launch_bounds__(BRT) k_seg_reduce(SegTab t, F f, double *parti
         float facc[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) facc[k] = 0.f;
+        // SU independent elements per step (BRT apart, so a warp's loads stay
+        // contiguous) keep enough loads in flight to cover HBM latency
         int c = 0;
-        for (long long e = start + threadIdx.x; e < end; e += BRT) {
-            f(e, s, facc);
-            if (++c == BCH32) {
+        long long e = start + threadIdx.x;
+        for (; e + (SU - 1) * BRT < end; e += SU * BRT) {
+#pragma unroll
+            for (int u = 0; u < SU; ++u) f(e + u * BRT, s, facc);
+            c += SU;
+            if (c >= BCH32) {
                 c = 0;
 #pragma unroll
                 for (int k = 0; k < NV; ++k) {
@@ -125,10 +131,15 @@ __global__ void __launch_bounds__(BRT) k_seg_reduce(SegTab t, F f, double *parti
                 }
             }
         }
+        for (; e < end; e += BRT) f(e, s, facc);
 #pragma unroll
         for (int k = 0; k < NV; ++k) acc[k] += (double)facc[k];
     } else {
-        for (long long e = start + threadIdx.x; e < end; e += BRT) f(e, s, acc);
+        long long e = start + threadIdx.x;
+        for (; e + (SU - 1) * BRT < end; e += SU * BRT)
+#pragma unroll
+            for (int u = 0; u < SU; ++u) f(e + u * BRT, s, acc);
+        for (; e < end; e += BRT) f(e, s, acc);
     }
     bblock_reduce<NV>(acc, sh);
     if (threadIdx.x == 0)
@@ -160,7 +171,11 @@ __global__ void __launch_bounds__(BRT) k_seg_map(SegTab t, F f)
     int s;
     long long start, end;
     seg_range(t, s, start, end);
-    for (long long e = start + threadIdx.x; e < end; e += BRT) f(e, s);
+    long long e = start + threadIdx.x;
+    for (; e + (SU - 1) * BRT < end; e += SU * BRT)
+#pragma unroll
+        for (int u = 0; u < SU; ++u) f(e + u * BRT, s);
+    for (; e < end; e += BRT) f(e, s);
 }
 
 __device__ __forceinline__ void fdot(float *acc, float2 a, float2 b)
