@@ -21,7 +21,6 @@
 namespace mgc {
 namespace {
 
-constexpr int MAXN = MGC_MG_MAX_NVEC;
 constexpr int CHUNK = 8;    // null vectors per restriction pass
 constexpr int CRT = 256;    // threads of the coarse reductions
 constexpr int CRG = 64;     // blocks of the coarse reductions

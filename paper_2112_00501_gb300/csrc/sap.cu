@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_sap_colour(Geom g, SP b, SP x, GA U, CL
                                                     int colour, int nmr, int x_zero)
 {
     using T = typename SP::Real;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int vb = 1 << g.lvb;
     Cx<T> *rs = reinterpret_cast<Cx<T> *>(smem);
     T *red = reinterpret_cast<T *>(rs + 12 * vb);

@@ -616,7 +616,7 @@ static int mg_precondition(mgc_mg_s *M, const mgc_mg_params *mp, const double2 *
     SolverWork *W = op->work;
     const long long n = (long long)op->gauge->lat->g.V * 12;
     MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, v[e]); }, W, W->scal + S_NW, s, 1));
-    double nn;
+    double nn = 0.0;
     MGC_TRY(read_scalar(W, S_NW, &nn, s));
     if (bad(nn)) return fail(MGC_ERR_BREAKDOWN, "multigrid: non-finite vector");
     return mg_precond64(M, mp, v, z, std::sqrt(nn), s);
