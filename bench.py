@@ -339,10 +339,12 @@ def bench_mg(lib, stream, op, b, params, w):
     mg = api.Multigrid(op, MG_AGG, MG_NVEC)
     mp = api.mg_params(n_cy=2, n_jacobi=4, smoother_prec=w["prec"], coarse_tol=5e-2, coarse_maxit=100, n_adapt=4)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("mg_setup")  # lets a profiler select these launches
     t0 = time.perf_counter()
     mg.setup(eta, mp)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
     del eta
     ps = api.solve_params(tol=w["tol"], max_iter=500)
     x, info = mg.solve(b, ps, mp)

@@ -22,6 +22,7 @@ namespace mgc {
 namespace {
 
 constexpr int CHUNK = 8;    // null vectors per restriction pass
+constexpr int RWARPS = 8;   // aggregates (one warp each) per restriction block
 constexpr int CRT = 256;    // threads of the coarse reductions
 constexpr int CRG = 64;     // blocks of the coarse reductions
 
@@ -73,6 +74,16 @@ __device__ __forceinline__ void coarse_coords(const MgGeom &m, int a, int ac[4])
     }
 }
 
+// whether fine site c lies on the face of its aggregate that coarse stencil
+// entry k >= 1 crosses (the +mu face for k = 1 + 2 mu, the -mu face for
+// k = 2 + 2 mu): the only sites where that entry's field is nonzero
+__device__ __forceinline__ bool on_face(const MgGeom &m, const int c[4], int k)
+{
+    const int mu = (k - 1) / 2;
+    const int A = m.ratio[mu] << m.g.lb[mu];  // aggregate extent along mu
+    return ((k - 1) % 2 == 0) ? ((c[mu] + 1) % A == 0) : (c[mu] % A == 0);
+}
+
 __device__ __forceinline__ int aggregate_of(const MgGeom &m, int i)
 {
     int bc[4], ac[4];
@@ -106,15 +117,21 @@ __device__ __forceinline__ void cdot4(float &re, float &im, float4 a, float4 b)
 
 // ------------------------------------------------------------------ restriction
 // out[a][chi][j] = sum_{x in a} conj(W_j(x))_chi . v(x)_chi for the vectors
-// j0 .. j0 + CHUNK - 1; one thread block per (aggregate, chunk), one thread per
-// domain site.  With colq >= 0 the result goes to column colq of the coarse
-// stencil entry k instead (Dc[a][k][colq][row]).
-__global__ void k_restrict(MgGeom m, const float4 *W, const float4 *v, float2 *out, float2 *Dc, int k, int colq)
+// j0 .. j0 + CHUNK - 1; one warp per (aggregate, chunk), RWARPS aggregates per
+// thread block.  With colq >= 0 the result goes to column colq of the coarse
+// stencil entry k instead (Dc[a][k][colq][row]), and for k >= 1 only the face
+// sites where that entry's field lives are read.
+__global__ void __launch_bounds__(RWARPS * 32) k_restrict(MgGeom m, const float4 *W, const float4 *v, float2 *out,
+                                                          float2 *Dc, int k, int colq)
 {
-    extern __shared__ float red[];  // [nwarps][2 * CHUNK * 2]
-    const int a = blockIdx.x, j0 = blockIdx.y * CHUNK;
-    const int l = threadIdx.x;
+    // one warp per aggregate: each lane takes every 32nd site of it and keeps
+    // the 2 x CHUNK complex sums, reduced across the warp once at the end
+    const int lane = threadIdx.x & 31;
+    const int a = blockIdx.x * RWARPS + (threadIdx.x >> 5);
+    if (a >= m.Vc) return;
+    const int j0 = blockIdx.y * CHUNK;
     const size_t fs = (size_t)m.g.V * 6;  // float4 per field
+    const int vb = 1 << m.g.lvb;
     int ac[4];
     coarse_coords(m, a, ac);
     float acc[2][CHUNK][2];
@@ -122,39 +139,47 @@ __global__ void k_restrict(MgGeom m, const float4 *W, const float4 *v, float2 *o
     for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int j = 0; j < CHUNK; ++j) acc[c][j][0] = acc[c][j][1] = 0.f;
+    const bool face = colq >= 0 && k >= 1;  // a coarse-operator column's face field
     for (int d = 0; d < m.da; ++d) {
-        const int i = (agg_domain(m, ac, d) << m.g.lvb) | l;
-        float4 vv[6];
+        const int base = agg_domain(m, ac, d) << m.g.lvb;
+        for (int l = lane; l < vb; l += 32) {
+            const int i = base | l;
+            if (face) {
+                int c[4];
+                site_coords(m.g, i, c);
+                if (!on_face(m, c, k)) continue;  // the field is zero there
+            }
+            float4 vv[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) vv[q] = __ldg(plane(v, m.g, i, q));
+            for (int q = 0; q < 6; ++q) vv[q] = __ldg(plane(v, m.g, i, q));
 #pragma unroll
-        for (int j = 0; j < CHUNK; ++j) {
-            if (j0 + j >= m.nvec) break;
-            const float4 *w = W + (j0 + j) * fs;
+            for (int j = 0; j < CHUNK; ++j) {
+                if (j0 + j >= m.nvec) break;
+                const float4 *w = W + (j0 + j) * fs;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) cdot4(acc[q / 3][j][0], acc[q / 3][j][1], __ldg(plane(w, m.g, i, q)), vv[q]);
+                for (int q = 0; q < 6; ++q)
+                    cdot4(acc[q / 3][j][0], acc[q / 3][j][1], __ldg(plane(w, m.g, i, q)), vv[q]);
+            }
         }
     }
-    // block reduction of the 2 x CHUNK complex sums
+    // butterfly sums leave every total in every lane; lane t stores sum t
     constexpr int NVAL = 2 * CHUNK * 2;
+    static_assert(NVAL == 32, "one sum per lane");
     float *flat = &acc[0][0][0];
+    float mine = 0.f;
 #pragma unroll
-    for (int t = 0; t < NVAL; ++t) flat[t] = warp_sum(flat[t]);
-    const int warp = l >> 5, lane = l & 31, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0)
+    for (int t = 0; t < NVAL; ++t) {
+        float x = flat[t];
 #pragma unroll
-        for (int t = 0; t < NVAL; ++t) red[warp * NVAL + t] = flat[t];
-    __syncthreads();
-    for (int t = l; t < NVAL; t += blockDim.x) {
-        float s = 0.f;
-        for (int w = 0; w < nw; ++w) s += red[w * NVAL + t];
-        const int chi = t / (2 * CHUNK), j = (t / 2) % CHUNK, ri = t & 1;
-        if (j0 + j < m.nvec) {
-            const int row = chi * m.nvec + j0 + j;
-            float *dst = colq < 0 ? reinterpret_cast<float *>(out + (size_t)a * m.n2 + row)
-                                  : reinterpret_cast<float *>(Dc + (((size_t)a * 9 + k) * m.n2 + colq) * m.n2 + row);
-            dst[ri] = s;
-        }
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (t == lane) mine = x;
+    }
+    const int chi = lane / (2 * CHUNK), j = (lane / 2) % CHUNK, ri = lane & 1;
+    if (j0 + j < m.nvec) {
+        const int row = chi * m.nvec + j0 + j;
+        float *dst = colq < 0 ? reinterpret_cast<float *>(out + (size_t)a * m.n2 + row)
+                              : reinterpret_cast<float *>(Dc + (((size_t)a * 9 + k) * m.n2 + colq) * m.n2 + row);
+        dst[ri] = mine;
     }
 }
 
@@ -290,6 +315,9 @@ __global__ void k_stencil_field(MgGeom m, Chiral32 p, GA U, Clover32 C, float ka
     const Geom &g = m.g;
     int c[4];
     site_coords(g, i, c);
+    // entries k >= 1 are zero off their face; the restriction of the column
+    // reads face sites only, so nothing is stored elsewhere
+    if (k >= 1 && !on_face(m, c, k)) return;
     Cx<float> acc[12];
 #pragma unroll
     for (int q = 0; q < 12; ++q) acc[q] = Cx<float>{0.f, 0.f};
@@ -577,14 +605,22 @@ int fnorm2(mgc_mg_s *M, const float4 *v, double *out, cudaStream_t s)
     return read_scalars(M, 1, out, s);
 }
 
+// fraction of the fine sites a coarse-operator column's field occupies: all
+// for the local entry k = 0, one face layer of each aggregate for k >= 1
+static double field_fraction(const MgGeom &m, int k)
+{
+    if (k == 0) return 1.0;
+    const int mu = (k - 1) / 2;
+    return 1.0 / (double)(m.ratio[mu] << m.g.lb[mu]);
+}
+
 int do_restrict(mgc_mg_s *M, const float4 *v, float2 *u, cudaStream_t s, int k = 0, int colq = -1)
 {
-    const int vb = 1 << M->m.g.lvb;
-    const int nw = (vb + 31) / 32;
-    dim3 grid(M->m.Vc, (M->m.nvec + CHUNK - 1) / CHUNK);
-    k_restrict<<<grid, vb, nw * 2 * CHUNK * 2 * sizeof(float), s>>>(M->m, M->w.W, v, u, M->w.Dc, k, colq);
+    dim3 grid((M->m.Vc + RWARPS - 1) / RWARPS, (M->m.nvec + CHUNK - 1) / CHUNK);
+    k_restrict<<<grid, RWARPS * 32, 0, s>>>(M->m, M->w.W, v, u, M->w.Dc, k, colq);
     MGC_CUDA(cudaGetLastError());
-    count(1, (double)fine32_bytes(M) * (M->m.nvec + grid.y));
+    const double frac = colq >= 0 ? field_fraction(M->m, k) : 1.0;
+    count(1, (double)fine32_bytes(M) * (M->m.nvec + grid.y) * frac);
     return MGC_OK;
 }
 
@@ -633,8 +669,8 @@ int build(mgc_mg_s *M, cudaStream_t s)
                     k_stencil_field<<<grid_for(g.V, 256), 256, 0, s>>>(
                         M->m, p, Gauge32x18{(float2 *)op->gauge->U32, g.lvb}, C, kappa, k, w.f0);
                 MGC_CUDA(cudaGetLastError());
-                count(1, (double)g.V * (96.0 * 2 + links_site_bytes(32, op->gauge->compress) +
-                                        clover_site_bytes(32)));
+                count(1, (double)g.V * field_fraction(M->m, k) *
+                             (96.0 * 2 + links_site_bytes(32, op->gauge->compress) + clover_site_bytes(32)));
                 MGC_TRY(do_restrict(M, w.f0, nullptr, s, k, chi * M->m.nvec + i));
             }
         }
