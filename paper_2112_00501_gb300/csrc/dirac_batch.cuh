@@ -37,8 +37,17 @@ template <class SP, class GA, class CL> struct DiracBatch {
     typename SP::Real kappa[MGC_BATCH_MAX];
 };
 
+// blocks per SM the register budget is set for: FP32 arithmetic with one RHS
+// per thread fits 80 registers (three 256-thread blocks), two RHS 128 (two);
+// four RHS and FP64 take one
+template <int RB, class SP>
+__host__ __device__ constexpr int dirac_batch_min_blocks()
+{
+    return sizeof(typename SP::Real) == 8 ? 1 : (RB == 1 ? 3 : (RB == 2 ? 2 : 1));
+}
+
 template <bool DAG, int LVB, int RB, class SP, class GA, class CL>
-__global__ void __launch_bounds__(256, 1) k_dirac_batch(DiracBatch<SP, GA, CL> B)
+__global__ void __launch_bounds__(256, dirac_batch_min_blocks<RB, SP>()) k_dirac_batch(DiracBatch<SP, GA, CL> B)
 {
     using T = typename SP::Real;
     int k = 0;
