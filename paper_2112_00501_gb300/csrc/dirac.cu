@@ -297,9 +297,10 @@ int launch_dirac_from16(const mgc_clover_s *op, const void *in16, void *out32, c
 
 // ------------------------------------------------------------------ A = C^-1 D
 // QWS's clover-preconditioned operator (Sec. 2): A psi = psi - kappa C^-1 H psi,
-// one thread per site, the same hopping sum as k_dirac followed by C^-1.
+// one thread per site, the same hopping sum as k_dirac followed by C^-1, in
+// k_dirac's launch shape.
 template <int LVB, class SP, class GA, class CL>
-__global__ void __launch_bounds__(256, (LVB > 0 && sizeof(typename SP::Real) == 4) ? 3 : 1)
+__global__ void __launch_bounds__(DIRAC_THREADS, (LVB > 0 && sizeof(typename SP::Real) == 4) ? 5 : 1)
     k_apply_A(Geom g, SP in, SP out, GA U, CL Ci, typename SP::Real kappa)
 {
     using T = typename SP::Real;
@@ -332,10 +333,10 @@ static void apply_A_dispatch(const Geom &g, SP in, SP out, GA U, CL Ci, double k
 {
     using T = typename SP::Real;
     const bool cube = g.lb[0] == g.lb[1] && g.lb[1] == g.lb[2] && g.lb[2] == g.lb[3];
-    dim3 grid(grid_for(g.V, 256), nrhs);
-    if (cube && g.lvb == 8) k_apply_A<8><<<grid, 256, 0, s>>>(g, in, out, U, Ci, (T)kappa);
-    else if (cube && g.lvb == 4) k_apply_A<4><<<grid, 256, 0, s>>>(g, in, out, U, Ci, (T)kappa);
-    else k_apply_A<0><<<grid, 256, 0, s>>>(g, in, out, U, Ci, (T)kappa);
+    dim3 grid(grid_for(g.V, DIRAC_THREADS), nrhs);
+    if (cube && g.lvb == 8) k_apply_A<8><<<grid, DIRAC_THREADS, 0, s>>>(g, in, out, U, Ci, (T)kappa);
+    else if (cube && g.lvb == 4) k_apply_A<4><<<grid, DIRAC_THREADS, 0, s>>>(g, in, out, U, Ci, (T)kappa);
+    else k_apply_A<0><<<grid, DIRAC_THREADS, 0, s>>>(g, in, out, U, Ci, (T)kappa);
 }
 
 int launch_apply_A(const mgc_clover_s *op, int prec, const void *in, void *out, int nrhs, cudaStream_t s)
