@@ -121,9 +121,12 @@ __device__ __forceinline__ void cdot4(float &re, float &im, float4 a, float4 b)
 // thread block.  With colq >= 0 the result goes to column colq of the coarse
 // stencil entry k instead (Dc[a][k][colq][row]), and for k >= 1 only the face
 // sites where that entry's field lives are read.
-__global__ void __launch_bounds__(RWARPS * 32) k_restrict(MgGeom m, const float4 *W, const float4 *v, float2 *out,
-                                                          float2 *Dc, int k, int colq)
+template <int NCOL>
+__global__ void __launch_bounds__(RWARPS * 32) k_restrict(MgGeom m, const float4 *W, const float4 *v, const float4 *v2,
+                                                          float2 *out, float2 *Dc, int k, int colq)
 {
+    // NCOL = 2: two coarse-operator columns (fields v and v2, columns colq and
+    // colq + 1 of entry k) share each read of the basis
     // one warp per aggregate: each lane takes every 32nd site of it and keeps
     // the 2 x CHUNK complex sums, reduced across the warp once at the end
     const int lane = threadIdx.x & 31;
@@ -134,11 +137,13 @@ __global__ void __launch_bounds__(RWARPS * 32) k_restrict(MgGeom m, const float4
     const int vb = 1 << m.g.lvb;
     int ac[4];
     coarse_coords(m, a, ac);
-    float acc[2][CHUNK][2];
+    float acc[NCOL][2][CHUNK][2];
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int f = 0; f < NCOL; ++f)
 #pragma unroll
-        for (int j = 0; j < CHUNK; ++j) acc[c][j][0] = acc[c][j][1] = 0.f;
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int j = 0; j < CHUNK; ++j) acc[f][c][j][0] = acc[f][c][j][1] = 0.f;
     const bool face = colq >= 0 && k >= 1;  // a coarse-operator column's face field
     for (int d = 0; d < m.da; ++d) {
         const int base = agg_domain(m, ac, d) << m.g.lvb;
@@ -149,37 +154,48 @@ __global__ void __launch_bounds__(RWARPS * 32) k_restrict(MgGeom m, const float4
                 site_coords(m.g, i, c);
                 if (!on_face(m, c, k)) continue;  // the field is zero there
             }
-            float4 vv[6];
+            float4 vv[NCOL][6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) vv[q] = __ldg(plane(v, m.g, i, q));
+            for (int q = 0; q < 6; ++q) {
+                vv[0][q] = __ldg(plane(v, m.g, i, q));
+                if (NCOL == 2) vv[NCOL - 1][q] = __ldg(plane(v2, m.g, i, q));
+            }
 #pragma unroll
             for (int j = 0; j < CHUNK; ++j) {
                 if (j0 + j >= m.nvec) break;
                 const float4 *w = W + (j0 + j) * fs;
 #pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    cdot4(acc[q / 3][j][0], acc[q / 3][j][1], __ldg(plane(w, m.g, i, q)), vv[q]);
+                for (int q = 0; q < 6; ++q) {
+                    const float4 wq = __ldg(plane(w, m.g, i, q));
+#pragma unroll
+                    for (int f = 0; f < NCOL; ++f) cdot4(acc[f][q / 3][j][0], acc[f][q / 3][j][1], wq, vv[f][q]);
+                }
             }
         }
     }
-    // butterfly sums leave every total in every lane; lane t stores sum t
+    // butterfly sums leave every total in every lane; lane t stores sum t of
+    // each column
     constexpr int NVAL = 2 * CHUNK * 2;
     static_assert(NVAL == 32, "one sum per lane");
-    float *flat = &acc[0][0][0];
-    float mine = 0.f;
-#pragma unroll
-    for (int t = 0; t < NVAL; ++t) {
-        float x = flat[t];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (t == lane) mine = x;
-    }
     const int chi = lane / (2 * CHUNK), j = (lane / 2) % CHUNK, ri = lane & 1;
-    if (j0 + j < m.nvec) {
-        const int row = chi * m.nvec + j0 + j;
-        float *dst = colq < 0 ? reinterpret_cast<float *>(out + (size_t)a * m.n2 + row)
-                              : reinterpret_cast<float *>(Dc + (((size_t)a * 9 + k) * m.n2 + colq) * m.n2 + row);
-        dst[ri] = mine;
+#pragma unroll
+    for (int f = 0; f < NCOL; ++f) {
+        float *flat = &acc[f][0][0][0];
+        float mine = 0.f;
+#pragma unroll
+        for (int t = 0; t < NVAL; ++t) {
+            float x = flat[t];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (t == lane) mine = x;
+        }
+        if (j0 + j < m.nvec) {
+            const int row = chi * m.nvec + j0 + j;
+            float *dst = colq < 0
+                             ? reinterpret_cast<float *>(out + (size_t)a * m.n2 + row)
+                             : reinterpret_cast<float *>(Dc + (((size_t)a * 9 + k) * m.n2 + colq + f) * m.n2 + row);
+            dst[ri] = mine;
+        }
     }
 }
 
@@ -617,10 +633,21 @@ static double field_fraction(const MgGeom &m, int k)
 int do_restrict(mgc_mg_s *M, const float4 *v, float2 *u, cudaStream_t s, int k = 0, int colq = -1)
 {
     dim3 grid((M->m.Vc + RWARPS - 1) / RWARPS, (M->m.nvec + CHUNK - 1) / CHUNK);
-    k_restrict<<<grid, RWARPS * 32, 0, s>>>(M->m, M->w.W, v, u, M->w.Dc, k, colq);
+    k_restrict<1><<<grid, RWARPS * 32, 0, s>>>(M->m, M->w.W, v, nullptr, u, M->w.Dc, k, colq);
     MGC_CUDA(cudaGetLastError());
     const double frac = colq >= 0 ? field_fraction(M->m, k) : 1.0;
     count(1, (double)fine32_bytes(M) * (M->m.nvec + grid.y) * frac);
+    return MGC_OK;
+}
+
+// columns colq and colq + 1 of coarse stencil entry k from their fields v, v2
+// in one pass over the basis
+int do_restrict2(mgc_mg_s *M, const float4 *v, const float4 *v2, cudaStream_t s, int k, int colq)
+{
+    dim3 grid((M->m.Vc + RWARPS - 1) / RWARPS, (M->m.nvec + CHUNK - 1) / CHUNK);
+    k_restrict<2><<<grid, RWARPS * 32, 0, s>>>(M->m, M->w.W, v, v2, nullptr, M->w.Dc, k, colq);
+    MGC_CUDA(cudaGetLastError());
+    count(1, (double)fine32_bytes(M) * (M->m.nvec + 2 * grid.y) * field_fraction(M->m, k));
     return MGC_OK;
 }
 
@@ -658,22 +685,32 @@ int build(mgc_mg_s *M, cudaStream_t s)
     const Clover32 C{(float4 *)op->C32, g.lvb};
     const float kappa = (float)op->kappa;
     const size_t fs = (size_t)g.V * 6;
+    auto field = [&](int chi, int i, int k, float4 *H) -> int {
+        const Chiral32 p{Spinor32{w.W + i * fs, g.lvb}, chi};
+        if (op->gauge->compress == 12)
+            k_stencil_field<<<grid_for(g.V, 256), 256, 0, s>>>(M->m, p, Gauge32x12{(float4 *)op->gauge->U32, g.lvb},
+                                                               C, kappa, k, H);
+        else
+            k_stencil_field<<<grid_for(g.V, 256), 256, 0, s>>>(M->m, p, Gauge32x18{(float2 *)op->gauge->U32, g.lvb},
+                                                               C, kappa, k, H);
+        MGC_CUDA(cudaGetLastError());
+        count(1, (double)g.V * field_fraction(M->m, k) *
+                     (96.0 * 2 + links_site_bytes(32, op->gauge->compress) + clover_site_bytes(32)));
+        return MGC_OK;
+    };
+    // columns (chi, i) and (chi, i + 1) of each entry share a pass over the basis
     for (int chi = 0; chi < 2; ++chi)
-        for (int i = 0; i < M->m.nvec; ++i) {
-            const Chiral32 p{Spinor32{w.W + i * fs, g.lvb}, chi};
+        for (int i = 0; i < M->m.nvec; i += 2)
             for (int k = 0; k < 9; ++k) {
-                if (op->gauge->compress == 12)
-                    k_stencil_field<<<grid_for(g.V, 256), 256, 0, s>>>(
-                        M->m, p, Gauge32x12{(float4 *)op->gauge->U32, g.lvb}, C, kappa, k, w.f0);
-                else
-                    k_stencil_field<<<grid_for(g.V, 256), 256, 0, s>>>(
-                        M->m, p, Gauge32x18{(float2 *)op->gauge->U32, g.lvb}, C, kappa, k, w.f0);
-                MGC_CUDA(cudaGetLastError());
-                count(1, (double)g.V * field_fraction(M->m, k) *
-                             (96.0 * 2 + links_site_bytes(32, op->gauge->compress) + clover_site_bytes(32)));
-                MGC_TRY(do_restrict(M, w.f0, nullptr, s, k, chi * M->m.nvec + i));
+                const int col = chi * M->m.nvec + i;
+                MGC_TRY(field(chi, i, k, w.f0));
+                if (i + 1 < M->m.nvec) {
+                    MGC_TRY(field(chi, i + 1, k, w.f1));
+                    MGC_TRY(do_restrict2(M, w.f0, w.f1, s, k, col));
+                } else {
+                    MGC_TRY(do_restrict(M, w.f0, nullptr, s, k, col));
+                }
             }
-        }
     M->ready = 1;
     return MGC_OK;
 }
