@@ -463,11 +463,11 @@ __device__ __forceinline__ double2 cs_omega(const double *sc)
 }
 
 template <int NV>
-__global__ void k_cfinish(const double *partial, double *out)
+__global__ void k_cfinish(const double *partial, double *out, int nblk = CRG)
 {
     if (threadIdx.x >= NV) return;
     double s = 0;
-    for (int b = 0; b < CRG; ++b) s += partial[b * NV + threadIdx.x];
+    for (int b = 0; b < nblk; ++b) s += partial[b * NV + threadIdx.x];
     out[threadIdx.x] = s;
 }
 
@@ -509,13 +509,28 @@ __global__ void k_fscale(long long n4, float s, float4 *v)
         v[e] = make_float4(s * x.x, s * x.y, s * x.z, s * x.w);
     }
 }
+// ||v||^2 of a fine FP32 field: FNG blocks (every SM busy, within the
+// partial area of CRG * 4 doubles), FP32 partial sums over four float4 per
+// step, FP64 beyond
+constexpr int FNG = CRG * 4;
 __global__ void __launch_bounds__(CRT) k_fnorm2(long long n4, const float4 *v, double *partial)
 {
     __shared__ double sh[CRT / 32];
     double acc = 0;
-    for (long long e = blockIdx.x * (long long)CRT + threadIdx.x; e < n4; e += (long long)gridDim.x * CRT) {
+    const long long stride = (long long)gridDim.x * CRT;
+    long long e = blockIdx.x * (long long)CRT + threadIdx.x;
+    for (; e + 3 * stride < n4; e += 4 * stride) {
+        float f = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 x = v[e + u * stride];
+            f = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, f))));
+        }
+        acc += (double)f;
+    }
+    for (; e < n4; e += stride) {
         const float4 x = v[e];
-        acc += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
+        acc += (double)fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, x.w * x.w)));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -614,8 +629,8 @@ int cmap(mgc_mg_s *M, F f, cudaStream_t s)
 
 int fnorm2(mgc_mg_s *M, const float4 *v, double *out, cudaStream_t s)
 {
-    k_fnorm2<<<CRG, CRT, 0, s>>>(fine4(M), v, M->w.partial);
-    k_cfinish<1><<<1, 32, 0, s>>>(M->w.partial, M->w.scal);
+    k_fnorm2<<<FNG, CRT, 0, s>>>(fine4(M), v, M->w.partial);
+    k_cfinish<1><<<1, 32, 0, s>>>(M->w.partial, M->w.scal, FNG);
     MGC_CUDA(cudaGetLastError());
     count(2, (double)fine32_bytes(M));
     return read_scalars(M, 1, out, s);
