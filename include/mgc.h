@@ -227,14 +227,14 @@ int mgc_sap_smooth_A(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy
  *      n_mr Jacobi iterations per domain) to inner_tol; x += ||C^-1 r|| M_SAP y.
  */
 typedef struct {
-    int method;        /* 0, 1 or 2 (above) */
+    int method;        /* 0, 1, 2 or 3 (above) */
     int precond;       /* 0 = none, 1 = SAP */
     int smoother_prec; /* 64, 32 or 16 (needs a copy at that precision; 32/16 for method 2) */
     int n_cy;          /* SAP sweeps per preconditioner application */
     int n_mr;          /* MR steps per domain */
     int restart;       /* FGCR length m (<= 32); method 2: inner iterations per pass */
     double tol;        /* stop when ||b - D x|| <= tol ||b||, D in FP64 */
-    int max_iter;      /* preconditioner applications (methods 0, 2), BiCGStab iterations (1) */
+    int max_iter;      /* preconditioner applications (methods 0, 2), BiCGStab iterations (1, 3) */
     int on_device;     /* 1: b, x are device pointers; 0: host pointers */
     int x_is_guess;    /* 1: x holds the initial guess; 0: start from x = 0 */
     double inner_tol;  /* method 2: relative residual reduction of each inner solve */
