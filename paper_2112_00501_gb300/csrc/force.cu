@@ -103,22 +103,43 @@ __global__ void k_force_N(Geom g, Spinor64 X, Spinor64 Y, double2 *N)
     }
 }
 
-// R = N0 M1 M2 M3 + M1 N1 M2 M3 + M1 M2 N2 M3 + M1 M2 M3 N3
-__device__ void corner_sum(const cd *M1, const cd *M2, const cd *M3, const cd *N0, const cd *N1, const cd *N2,
-                           const cd *N3, cd *R)
+
+// where a factor of a plaquette term sits relative to site c: a link
+// (shifts along d0, d1; its direction; daggered or not) or an insertion N
+struct LinkRef {
+    int d0, s0, d1, s1, dir;
+    bool dag;
+};
+struct NRef {
+    int d0, s0, d1, s1;
+};
+
+// R = N0 M1 M2 M3 + M1 N1 M2 M3 + M1 M2 N2 M3 + M1 M2 M3 N3 with shared
+// prefixes, each factor loaded just before its product, so that four 3x3
+// matrices are live at a time (preloading all seven factors made the kernel
+// spill)
+__device__ void corner_sum(const Gauge64 &U, const double2 *N, const Geom &g, const int c[4], int p,
+                                const LinkRef m[3], const NRef n[4], cd *R)
 {
-    cd T[9], P[9], Q[9];
-    f_m3mul(N0, M1, T);
-    f_m3mul(M1, N1, Q);
-    for (int k = 0; k < 9; ++k) T[k] = T[k] + Q[k];       // N0 M1 + M1 N1
-    f_m3mul(M1, M2, P);                                    // M1 M2
-    f_m3mul(T, M2, T);
-    f_m3mul(P, N2, Q);
-    for (int k = 0; k < 9; ++k) T[k] = T[k] + Q[k];       // (..) M2 + M1 M2 N2
-    f_m3mul(P, M3, P);                                     // M1 M2 M3
-    f_m3mul(T, M3, T);
-    f_m3mul(P, N3, Q);
-    for (int k = 0; k < 9; ++k) R[k] = T[k] + Q[k];
+    cd A[9], B[9], T[9], P[9];
+    f_link(U, g, c, m[0].d0, m[0].s0, m[0].d1, m[0].s1, m[0].dir, m[0].dag, A);  // M1
+    f_N(N, g, c, n[0].d0, n[0].s0, n[0].d1, n[0].s1, p, B);
+    f_m3mul(B, A, T);  // N0 M1
+    f_N(N, g, c, n[1].d0, n[1].s0, n[1].d1, n[1].s1, p, B);
+    f_m3mul(A, B, P);
+    for (int k = 0; k < 9; ++k) T[k] = T[k] + P[k];  // N0 M1 + M1 N1
+    f_link(U, g, c, m[1].d0, m[1].s0, m[1].d1, m[1].s1, m[1].dir, m[1].dag, B);  // M2
+    f_m3mul(A, B, P);  // M1 M2
+    f_m3mul(T, B, A);  // (..) M2
+    f_N(N, g, c, n[2].d0, n[2].s0, n[2].d1, n[2].s1, p, B);
+    f_m3mul(P, B, T);
+    for (int k = 0; k < 9; ++k) T[k] = A[k] + T[k];  // (..) M2 + M1 M2 N2
+    f_link(U, g, c, m[2].d0, m[2].s0, m[2].d1, m[2].s1, m[2].dir, m[2].dag, B);  // M3
+    f_m3mul(P, B, A);  // M1 M2 M3
+    f_m3mul(T, B, P);  // (..) M3
+    f_N(N, g, c, n[3].d0, n[3].s0, n[3].d1, n[3].s1, p, B);
+    f_m3mul(A, B, T);  // M1 M2 M3 N3
+    for (int k = 0; k < 9; ++k) R[k] = P[k] + T[k];
 }
 
 __device__ __forceinline__ int plane_of(int a, int b)
@@ -177,51 +198,33 @@ __global__ void k_force(Geom g, Gauge64 U, Spinor64 X, Spinor64 Y, const double2
     for (int sgm = 0; sgm < 4; ++sgm) {
         if (sgm == mu) continue;
         const int p = plane_of(mu, sgm);
-        cd M1[9], M2[9], M3[9], N0[9], N1[9], N2[9], N3[9], R[9];
+        cd R[9];
         // undaggered plaquette
         if (mu < sgm) {
             // U_mu(y) U_s(y+mu) U_mu(y+s)^+ U_s(y)^+
-            f_link(U, g, c, mu, 1, sgm, 0, sgm, false, M1);
-            f_link(U, g, c, mu, 0, sgm, 1, mu, true, M2);
-            f_link(U, g, c, mu, 0, sgm, 0, sgm, true, M3);
-            f_N(N, g, c, mu, 1, sgm, 0, p, N0);
-            f_N(N, g, c, mu, 1, sgm, 1, p, N1);
-            f_N(N, g, c, mu, 0, sgm, 1, p, N2);
-            f_N(N, g, c, mu, 0, sgm, 0, p, N3);
+            const LinkRef m[3] = {{mu, 1, sgm, 0, sgm, false}, {mu, 0, sgm, 1, mu, true}, {mu, 0, sgm, 0, sgm, true}};
+            const NRef n[4] = {{mu, 1, sgm, 0}, {mu, 1, sgm, 1}, {mu, 0, sgm, 1}, {mu, 0, sgm, 0}};
+            corner_sum(U, N, g, c, p, m, n, R);
         } else {
             // U_s(y-s) U_mu(y) U_s(y-s+mu)^+ U_mu(y-s)^+
-            f_link(U, g, c, sgm, -1, mu, 1, sgm, true, M1);
-            f_link(U, g, c, sgm, -1, mu, 0, mu, true, M2);
-            f_link(U, g, c, sgm, -1, mu, 0, sgm, false, M3);
-            f_N(N, g, c, sgm, 0, mu, 1, p, N0);
-            f_N(N, g, c, sgm, -1, mu, 1, p, N1);
-            f_N(N, g, c, sgm, -1, mu, 0, p, N2);
-            f_N(N, g, c, sgm, 0, mu, 0, p, N3);
+            const LinkRef m[3] = {{sgm, -1, mu, 1, sgm, true}, {sgm, -1, mu, 0, mu, true}, {sgm, -1, mu, 0, sgm, false}};
+            const NRef n[4] = {{sgm, 0, mu, 1}, {sgm, -1, mu, 1}, {sgm, -1, mu, 0}, {sgm, 0, mu, 0}};
+            corner_sum(U, N, g, c, p, m, n, R);
         }
-        corner_sum(M1, M2, M3, N0, N1, N2, N3, R);
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) G[a * 3 + b] = G[a * 3 + b] + cpc * conj(R[b * 3 + a]);
         // daggered plaquette
         if (mu < sgm) {
             // U_mu(y-s) U_s(y-s+mu) U_mu(y)^+ U_s(y-s)^+ ; after the link: y -> y-s -> y-s+mu -> y+mu
-            f_link(U, g, c, mu, 0, sgm, -1, sgm, true, M1);
-            f_link(U, g, c, mu, 0, sgm, -1, mu, false, M2);
-            f_link(U, g, c, mu, 1, sgm, -1, sgm, false, M3);
-            f_N(N, g, c, mu, 0, sgm, 0, p, N0);
-            f_N(N, g, c, mu, 0, sgm, -1, p, N1);
-            f_N(N, g, c, mu, 1, sgm, -1, p, N2);
-            f_N(N, g, c, mu, 1, sgm, 0, p, N3);
+            const LinkRef m[3] = {{mu, 0, sgm, -1, sgm, true}, {mu, 0, sgm, -1, mu, false}, {mu, 1, sgm, -1, sgm, false}};
+            const NRef n[4] = {{mu, 0, sgm, 0}, {mu, 0, sgm, -1}, {mu, 1, sgm, -1}, {mu, 1, sgm, 0}};
+            corner_sum(U, N, g, c, p, m, n, R);
         } else {
             // U_s(y) U_mu(y+s) U_s(y+mu)^+ U_mu(y)^+ ; after the link: y -> y+s -> y+s+mu -> y+mu
-            f_link(U, g, c, sgm, 0, mu, 0, sgm, false, M1);
-            f_link(U, g, c, sgm, 1, mu, 0, mu, false, M2);
-            f_link(U, g, c, sgm, 0, mu, 1, sgm, true, M3);
-            f_N(N, g, c, sgm, 0, mu, 0, p, N0);
-            f_N(N, g, c, sgm, 1, mu, 0, p, N1);
-            f_N(N, g, c, sgm, 1, mu, 1, p, N2);
-            f_N(N, g, c, sgm, 0, mu, 1, p, N3);
+            const LinkRef m[3] = {{sgm, 0, mu, 0, sgm, false}, {sgm, 1, mu, 0, mu, false}, {sgm, 0, mu, 1, sgm, true}};
+            const NRef n[4] = {{sgm, 0, mu, 0}, {sgm, 1, mu, 0}, {sgm, 1, mu, 1}, {sgm, 0, mu, 1}};
+            corner_sum(U, N, g, c, p, m, n, R);
         }
-        corner_sum(M1, M2, M3, N0, N1, N2, N3, R);
         for (int k = 0; k < 9; ++k) G[k] = G[k] + cp * R[k];
     }
     double2 *o = out + (canon_index(g, c) * 4 + mu) * 9;
