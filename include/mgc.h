@@ -254,6 +254,10 @@ void mgc_solve_params_default(mgc_solve_params *p);
  * Solve D x = b for nrhs canonical complex128 right-hand sides (one after the
  * other).  FP64 vectors, inner products, orthogonalisation and residual
  * updates; the SAP preconditioner in smoother_prec.  Synchronises stream.
+ * Host pointers (on_device = 0): with x in page-locked memory, method 2
+ * copies x back on a stream of its own while the FP64 residual that confirms
+ * convergence is computed; x holds the solution once the call returns, as
+ * with pageable x, and is not written after the return.
  */
 int mgc_solve(mgc_clover_t op, const double *b, double *x, int nrhs, const mgc_solve_params *p,
               mgc_solve_info *info, void *stream);

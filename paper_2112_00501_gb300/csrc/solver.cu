@@ -45,6 +45,12 @@ struct SolverWork {
     unsigned *counter = nullptr;
     double2 *stage = nullptr;   // canonical staging for host pointers
     double *hscal = nullptr;    // pinned host copy of a few scalars
+    // host-pointer solves into page-locked x: the canonical x can go to the
+    // host on copy_stream while the FP64 residual that confirms it is computed
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_x = nullptr, ev_copy = nullptr;
+    double *host_x = nullptr;   // the caller's x of the current solve, else null
+    bool copy_live = false;     // a copy of the current x to host_x is in flight
 };
 
 // device scalar slots
@@ -222,8 +228,12 @@ void free_work(mgc_clover_s *op)
     cudaFree(W->scal);
     cudaFree(W->partial);
     cudaFree(W->counter);
+    if (W->copy_live) cudaEventSynchronize(W->ev_copy);
     cudaFree(W->stage);
     cudaFreeHost(W->hscal);
+    if (W->ev_x) cudaEventDestroy(W->ev_x);
+    if (W->ev_copy) cudaEventDestroy(W->ev_copy);
+    if (W->copy_stream) cudaStreamDestroy(W->copy_stream);
     delete W;
     op->work = nullptr;
 }
@@ -279,7 +289,47 @@ static int ensure_work(mgc_clover_s *op, int method, int m, int lowprec)
     MGC_CUDA(cudaMemset(W->counter, 0, sizeof(unsigned)));
     MGC_CUDA(cudaMalloc(&W->stage, vb));
     MGC_CUDA(cudaMallocHost(&W->hscal, 2 * MAXM * sizeof(double)));
+    MGC_CUDA(cudaStreamCreateWithFlags(&W->copy_stream, cudaStreamNonBlocking));
+    MGC_CUDA(cudaEventCreateWithFlags(&W->ev_x, cudaEventDisableTiming));
+    MGC_CUDA(cudaEventCreateWithFlags(&W->ev_copy, cudaEventDisableTiming));
     return MGC_OK;
+}
+
+// x (canonical, through the staging buffer) to the caller's page-locked host
+// x: the unpack on s, the copy on the copy stream, where it overlaps whatever
+// s runs next
+static int copy_x_early(mgc_clover_s *op, cudaStream_t s)
+{
+    SolverWork *W = op->work;
+    const Geom &g = op->gauge->lat->g;
+    MGC_TRY(launch_unpack(g, 64, 1, W->x, (double *)W->stage, s));
+    MGC_CUDA(cudaEventRecord(W->ev_x, s));
+    MGC_CUDA(cudaStreamWaitEvent(W->copy_stream, W->ev_x, 0));
+    MGC_CUDA(cudaMemcpyAsync(W->host_x, W->stage, spinor_bytes(g, 64, 1), cudaMemcpyDeviceToHost, W->copy_stream));
+    MGC_CUDA(cudaEventRecord(W->ev_copy, W->copy_stream));
+    W->copy_live = true;
+    return MGC_OK;
+}
+
+// s waits for an early copy of x: the staging buffer is free again and the
+// host x complete once s reaches this point
+static int join_copy(SolverWork *W, cudaStream_t s)
+{
+    if (!W->copy_live) return MGC_OK;
+    W->copy_live = false;
+    MGC_CUDA(cudaStreamWaitEvent(s, W->ev_copy, 0));
+    return MGC_OK;
+}
+
+// page-locked host memory (a copy to pageable memory would not overlap)
+static bool page_locked(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
 }
 
 // the smoother as preconditioner (x = 0 on entry), with the domain solver p->sap_solver
@@ -1257,9 +1307,13 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
             for (int j = 0; j < k; ++j) Lz.p[j] = (const float4 *)W->z32[j];
             MGC_TRY(axpy_sum32(op, x, Lz, G, k, s));
         }
+        // the inner solve predicts that this x meets the tolerance: it goes to
+        // the host (host-pointer solves) while the FP64 residual checks it
+        if (W->host_x && rri <= tol2) MGC_TRY(copy_x_early(op, s));
         MGC_TRY(apply_D64(op, x, t, s));
         MGC_TRY(residual_to32(op, b, t, r32, rl, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
+        if (!(rr <= tol2)) MGC_TRY(join_copy(W, s));  // x changes again
         info->iters = iters;
         info->restarts++;
         MGC_TRY(check_device_status(op, s));
@@ -1602,15 +1656,23 @@ int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solv
             }
         }
         mgc_solve_info one{MGC_OK, 0, 0, 0.0};
+        W->host_x = (!p->on_device && page_locked(xk)) ? xk : nullptr;
         const int st = run_method(op, p, &one, s);
+        W->host_x = nullptr;
         if (st != MGC_OK && st != MGC_NOT_CONVERGED) {
+            // no copy into the caller's x may still run after the return
+            if (W->copy_live) cudaEventSynchronize(W->ev_copy);
+            W->copy_live = false;
             one.status = st;
             *info = one;
             return st;
         }
         if (p->on_device) {
             MGC_TRY(launch_unpack(g, 64, 1, W->x, xk, s));
+        } else if (W->copy_live && st == MGC_OK) {
+            MGC_TRY(join_copy(W, s));  // the converged x is on its way to the host
         } else {
+            MGC_TRY(join_copy(W, s));
             MGC_TRY(launch_unpack(g, 64, 1, W->x, (double *)W->stage, s));
             MGC_CUDA(cudaMemcpyAsync(xk, W->stage, vb, cudaMemcpyDeviceToHost, s));
         }

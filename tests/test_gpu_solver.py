@@ -64,6 +64,33 @@ def test_unpreconditioned_and_host_pointer_paths():
     assert np.array_equal(x2.numpy(), x3.cpu().numpy())
 
 
+def test_host_pointer_solves_match_device_solves():
+    """Host b and x: into page-locked x the converged iterate is copied while
+    the FP64 residual that confirms it is computed; into pageable x after the
+    solve.  Both give exactly the device-pointer solution, right-hand side by
+    right-hand side."""
+    from paper_2112_00501_gb300 import synth
+
+    name = "mid_8^4"
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    op = _op(name, 16, 12)
+    bs = synth.gaussian_spinor(dims, 702, nrhs=2)
+    xd, infod = op.solve(torch.from_numpy(bs).cuda(), smoother_prec=16)
+    assert infod.status == 0
+    xp, infop = op.solve(bs, smoother_prec=16)  # page-locked x
+    assert xp.is_pinned() and infop.status == 0 and infop.iters == infod.iters
+    assert np.array_equal(xp.numpy(), xd.cpu().numpy())
+    out = torch.zeros(xd.shape, dtype=torch.complex128)  # pageable x
+    xq, infoq = op.solve(bs, smoother_prec=16, out=out)
+    assert xq.data_ptr() == out.data_ptr() and infoq.status == 0
+    assert np.array_equal(xq.numpy(), xd.cpu().numpy())
+    # a tolerance the inner solve reaches only over several outer passes
+    xr, infor = op.solve(bs[0], smoother_prec=16, inner_tol=0.3, max_iter=400)
+    xs, infos = op.solve(torch.from_numpy(bs[0]).cuda(), smoother_prec=16, inner_tol=0.3, max_iter=400)
+    assert infor.status == 0 and infor.restarts > 2 and infor.restarts == infos.restarts
+    assert np.array_equal(xr.numpy(), xs.cpu().numpy())
+
+
 def test_multiple_rhs_and_initial_guess():
     from paper_2112_00501_gb300 import synth
 
