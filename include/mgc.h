@@ -257,7 +257,10 @@ void mgc_solve_params_default(mgc_solve_params *p);
  * Host pointers (on_device = 0): with x in page-locked memory, method 2
  * copies x back on a stream of its own while the FP64 residual that confirms
  * convergence is computed; x holds the solution once the call returns, as
- * with pageable x, and is not written after the return.
+ * with pageable x, and is not written after the return.  With several
+ * right-hand sides in page-locked b, the next b is copied to the device
+ * while the current one is solved (in a second 24 * 8 * V byte buffer of the
+ * operator's workspace); b is not read after the return.
  */
 int mgc_solve(mgc_clover_t op, const double *b, double *x, int nrhs, const mgc_solve_params *p,
               mgc_solve_info *info, void *stream);

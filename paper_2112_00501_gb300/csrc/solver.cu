@@ -51,6 +51,10 @@ struct SolverWork {
     cudaEvent_t ev_x = nullptr, ev_copy = nullptr;
     double *host_x = nullptr;   // the caller's x of the current solve, else null
     bool copy_live = false;     // a copy of the current x to host_x is in flight
+    // several host right-hand sides in page-locked memory: the next b crosses
+    // the host link into stage2 (copy stream, ev_b) during the current solve
+    double2 *stage2 = nullptr;
+    cudaEvent_t ev_b = nullptr;
 };
 
 // device scalar slots
@@ -228,11 +232,13 @@ void free_work(mgc_clover_s *op)
     cudaFree(W->scal);
     cudaFree(W->partial);
     cudaFree(W->counter);
-    if (W->copy_live) cudaEventSynchronize(W->ev_copy);
+    if (W->copy_stream) cudaStreamSynchronize(W->copy_stream);
     cudaFree(W->stage);
+    cudaFree(W->stage2);
     cudaFreeHost(W->hscal);
     if (W->ev_x) cudaEventDestroy(W->ev_x);
     if (W->ev_copy) cudaEventDestroy(W->ev_copy);
+    if (W->ev_b) cudaEventDestroy(W->ev_b);
     if (W->copy_stream) cudaStreamDestroy(W->copy_stream);
     delete W;
     op->work = nullptr;
@@ -292,6 +298,7 @@ static int ensure_work(mgc_clover_s *op, int method, int m, int lowprec)
     MGC_CUDA(cudaStreamCreateWithFlags(&W->copy_stream, cudaStreamNonBlocking));
     MGC_CUDA(cudaEventCreateWithFlags(&W->ev_x, cudaEventDisableTiming));
     MGC_CUDA(cudaEventCreateWithFlags(&W->ev_copy, cudaEventDisableTiming));
+    MGC_CUDA(cudaEventCreateWithFlags(&W->ev_b, cudaEventDisableTiming));
     return MGC_OK;
 }
 
@@ -1641,6 +1648,9 @@ int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solv
     const size_t vb = spinor_bytes(g, 64, 1);
     int worst = MGC_OK;
     mgc_solve_info agg{MGC_OK, 0, 0, 0.0};
+    const bool next_b = !p->on_device && nrhs > 1 && page_locked(b);
+    if (next_b && !W->stage2) MGC_CUDA(cudaMalloc(&W->stage2, vb));
+    bool b_waiting = false;  // stage2 receives this right-hand side's b (ev_b)
     for (int k = 0; k < nrhs; ++k) {
         const double *bk = b + (size_t)k * g.V * 24;
         double *xk = x + (size_t)k * g.V * 24;
@@ -1648,8 +1658,25 @@ int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solv
             MGC_TRY(launch_pack(g, 64, 1, bk, W->b, s));
             if (p->x_is_guess) MGC_TRY(launch_pack(g, 64, 1, xk, W->x, s));
         } else {
-            MGC_CUDA(cudaMemcpyAsync(W->stage, bk, vb, cudaMemcpyHostToDevice, s));
-            MGC_TRY(launch_pack(g, 64, 1, (const double *)W->stage, W->b, s));
+            const double2 *src = W->stage;
+            if (b_waiting) {
+                MGC_CUDA(cudaStreamWaitEvent(s, W->ev_b, 0));
+                src = W->stage2;
+                b_waiting = false;
+            } else {
+                MGC_CUDA(cudaMemcpyAsync(W->stage, bk, vb, cudaMemcpyHostToDevice, s));
+            }
+            MGC_TRY(launch_pack(g, 64, 1, (const double *)src, W->b, s));
+            if (next_b && k + 1 < nrhs) {
+                // the next b crosses the host link while this one is solved,
+                // into stage2 once the pack above has read it
+                MGC_CUDA(cudaEventRecord(W->ev_x, s));
+                MGC_CUDA(cudaStreamWaitEvent(W->copy_stream, W->ev_x, 0));
+                MGC_CUDA(cudaMemcpyAsync(W->stage2, bk + (size_t)g.V * 24, vb, cudaMemcpyHostToDevice,
+                                         W->copy_stream));
+                MGC_CUDA(cudaEventRecord(W->ev_b, W->copy_stream));
+                b_waiting = true;
+            }
             if (p->x_is_guess) {
                 MGC_CUDA(cudaMemcpyAsync(W->stage, xk, vb, cudaMemcpyHostToDevice, s));
                 MGC_TRY(launch_pack(g, 64, 1, (const double *)W->stage, W->x, s));
@@ -1660,8 +1687,8 @@ int solve(mgc_clover_s *op, const double *b, double *x, int nrhs, const mgc_solv
         const int st = run_method(op, p, &one, s);
         W->host_x = nullptr;
         if (st != MGC_OK && st != MGC_NOT_CONVERGED) {
-            // no copy into the caller's x may still run after the return
-            if (W->copy_live) cudaEventSynchronize(W->ev_copy);
+            // no copy from the caller's b or into its x may still run after the return
+            cudaStreamSynchronize(W->copy_stream);
             W->copy_live = false;
             one.status = st;
             *info = one;
