@@ -64,3 +64,28 @@ def test_host_side_argument_checks(lib):
     assert L.mgc_lattice_create(dims, ok_block, 0, ctypes.byref(h)) == _lib.MGC_ERR_INVALID_ARG
     assert b"t_bc" in L.mgc_last_error()
     assert L.mgc_status_string(_lib.MGC_ERR_TIMEOUT) == b"MGC_ERR_TIMEOUT"
+
+
+def test_product_path_is_independent_of_the_oracle():
+    """The package and its CUDA sources neither import, include nor link
+    anything under oracle/, and the oracle does not use the package beyond
+    the seeded input generators."""
+    pkg = os.path.join(ROOT, "paper_2112_00501_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if not f.endswith((".py", ".cu", ".cuh", ".h")):
+                continue
+            src = open(os.path.join(dirpath, f)).read()
+            assert not re.search(r"^\s*(from|import)\s+oracle\b", src, re.M), f
+            assert "liboracle" not in src and "oracle.c" not in src and "oracle.h" not in src, f
+    for f in ("oracle.py", "oracle.c", "build.py", "__init__.py"):
+        src = open(os.path.join(ROOT, "oracle", f)).read()
+        for m in re.finditer(r"paper_2112_00501_gb300\.?(\w*)", src):
+            assert m.group(1) in ("", "synth"), (f, m.group(0))
+    import subprocess
+    lib_path = os.path.join(pkg, "libmgc.so")
+    if os.path.exists(lib_path):
+        deps = subprocess.run(["ldd", lib_path], capture_output=True, text=True).stdout
+        assert "oracle" not in deps
