@@ -155,6 +155,14 @@ int mgc_device_status(mgc_clover_t op, int *flags, int clear, void *stream);
  * call returns MGC_ERR_TIMEOUT with the context still usable.
  */
 int mgc_selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, void *stream);
+/*
+ * Measured fused multiply-add rate of this GPU (no paper counterpart; the
+ * denominator of the roofline of the arithmetic-bound kernels): prec 32 (FP32
+ * FMA) or 64 (FP64 FMA).  Eight 256-thread blocks per SM, each thread running
+ * eight independent FMA chains; *flops_per_s receives 2 x FMAs / time of the
+ * fastest of five launches (about 10 ms each).  Synchronises stream.
+ */
+int mgc_fma_peak(int prec, double *flops_per_s, void *stream);
 /* C (inverse = 0) or C^-1 (inverse = 1) as canonical 12x12 complex128 per site (device). */
 int mgc_clover_export(mgc_clover_t op, int inverse, double *out, void *stream);
 
@@ -281,9 +289,13 @@ int mgc_solve(mgc_clover_t op, const double *b, double *x, int nrhs, const mgc_s
  * D and the smoother.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * The address is cached per device for the life of the process; after
+ * cudaDeviceReset (or any other teardown of the device's primary context) the
+ * cached address is stale and this entry point must not be called again.
  * All calls share the one array and it keeps the last call's contents; calls
  * that overlap on the GPU (other streams, other host threads) race on it and
- * must not be made.  Synchronises stream.
+ * must not be made: serialise calls from several host threads.  Synchronises
+ * stream.
  */
 #define MGC_NOALLOC_MAX_SITES 4096
 int mgc_solve_noalloc(mgc_clover_t op, const double *b, double *x, const mgc_solve_params *p, mgc_solve_info *info,
@@ -294,8 +306,12 @@ int mgc_solve_noalloc(mgc_clover_t op, const double *b, double *x, const mgc_sol
  * gamma5 D^-1 gamma5 phi) and D X = Y, then dS/dU from the hopping outer
  * products and the clover-leaf derivative.  phi: canonical complex128 (one
  * field, on_device as in p); dSdU: canonical [V][4][3][3] complex128 in the
- * same memory kind.  action (optional) receives S estimated as
- * 2 Re(phi^+ X) - ||D X||^2.  Synchronises stream.
+ * same memory kind.  action (optional, room for two doubles) receives S,
+ * estimated as 2 Re(phi^+ X) - ||D X||^2 (second order in the solver error),
+ * as the unevaluated sum action[0] + action[1]: action[0] is S rounded to
+ * double and action[1] the remainder, from exact products and double-double
+ * sums, so that the difference of two nearby actions keeps its digits (finite
+ * differences at small steps).  Synchronises stream.
  */
 int mgc_force(mgc_clover_t op, const double *phi, double *dSdU, const mgc_solve_params *p,
               mgc_solve_info *info, double *action, void *stream);

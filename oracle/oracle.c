@@ -185,6 +185,17 @@ int or_threads(void)
 #endif
 }
 
+/* thread count of the parallel loops that follow (n >= 1); the arithmetic of
+ * every loop is per site, so the results do not depend on it */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* 3x3 colour algebra                                                   */
 /* ------------------------------------------------------------------ */

@@ -33,6 +33,8 @@ def lib():
         L.or_gamma.argtypes = [_c16]
         L.or_sigma.argtypes = [_c16]
         L.or_threads.restype = C.c_int
+        L.or_set_threads.restype = None
+        L.or_set_threads.argtypes = [C.c_int]
         L.or_field_strength_site.argtypes = [_i4, _c16, C.c_long, _c16]
         L.or_clover_site.argtypes = [_i4, C.c_double, C.c_double, _c16, C.c_long, _c16]
         L.or_clover_build.argtypes = [_i4, C.c_double, C.c_double, _c16, _c16]
@@ -114,6 +116,11 @@ def _vb(bdims):
 def threads() -> int:
     """Number of OpenMP threads the oracle uses (1 without OpenMP)."""
     return int(lib().or_threads())
+
+
+def set_threads(n: int) -> None:
+    """Run the oracle's parallel loops on n threads from here on."""
+    lib().or_set_threads(int(n))
 
 
 def gamma():

@@ -278,18 +278,21 @@ class CloverOperator:
             check(st, "mgc_solve")
         return x, info
 
-    def force(self, phi, params: SolveParams | None = None, stream=None, **kw):
-        """dS/dU for S = phi^+ (D^+ D)^-1 phi; returns (g (V, 4, 3, 3) complex128, S, info)."""
+    def force(self, phi, params: SolveParams | None = None, stream=None, action_parts=False, **kw):
+        """dS/dU for S = phi^+ (D^+ D)^-1 phi; returns (g (V, 4, 3, 3) complex128, S, info).
+        With action_parts, S is the pair (S rounded to double, remainder)."""
         p = params if params is not None else solve_params(**kw)
         on_device = isinstance(phi, torch.Tensor) and phi.is_cuda
         ph = _canon(phi, "cuda" if on_device else "cpu")
         p.on_device = int(on_device)
         g = torch.empty((self.lattice.volume, 4, 3, 3), dtype=torch.complex128, device=ph.device)
         info = SolveInfo()
-        S = C.c_double(0)
-        check(self.lib.mgc_force(self.handle, _ptr(ph), _ptr(g), C.byref(p), C.byref(info), C.byref(S),
+        S = (C.c_double * 2)(0.0, 0.0)
+        check(self.lib.mgc_force(self.handle, _ptr(ph), _ptr(g), C.byref(p), C.byref(info), S,
                                  _stream(stream)), "mgc_force")
-        return g, float(S.value), info
+        if action_parts:
+            return g, (float(S[0]), float(S[1])), info
+        return g, float(S[0]), info
 
 
 def _ptr_array(ts):

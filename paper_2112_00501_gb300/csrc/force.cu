@@ -232,9 +232,12 @@ __global__ void k_force(Geom g, Gauge64 U, Spinor64 X, Spinor64 Y, const double2
 }
 
 // S = 2 Re <phi, X> - ||D X||^2.  The two sums are nearly equal (both ~S), and
-// finite-difference checks of S need it to ~1e-15 relative, so they are
-// accumulated as unevaluated double-double pairs (Knuth's TwoSum) and the
-// block partials are combined on the host the same way.
+// central differences of S at small steps need S well beyond double precision
+// (on 8^4, S ~ 5e4 has an ulp of 7e-12, which a step of 1e-5 turns into 4e-7
+// of a derivative), so every product is split exactly into a double and its
+// rounding error (fma), both are accumulated as unevaluated double-double
+// pairs (Knuth's TwoSum), and the block partials are combined on the host the
+// same way; S is returned as the pair (S rounded, remainder).
 __device__ __forceinline__ void two_sum_acc(double &hi, double &lo, double v)
 {
     const double s = hi + v;
@@ -244,16 +247,25 @@ __device__ __forceinline__ void two_sum_acc(double &hi, double &lo, double v)
     lo += err;
 }
 
+// hi + lo += a * b, with the product's rounding error carried in lo
+__device__ __forceinline__ void two_prod_acc(double &hi, double &lo, double a, double b)
+{
+    const double p = a * b;
+    const double e = fma(a, b, -p);
+    two_sum_acc(hi, lo, p);
+    lo += e;
+}
+
 __global__ void k_action_partial(long long n, const double2 *phi, const double2 *X, const double2 *DX, double *part)
 {
     __shared__ double sh[4][256];
     double ah = 0, al = 0, bh = 0, bl = 0;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const double2 p = phi[e], x = X[e], d = DX[e];
-        two_sum_acc(ah, al, p.x * x.x);
-        two_sum_acc(ah, al, p.y * x.y);
-        two_sum_acc(bh, bl, d.x * d.x);
-        two_sum_acc(bh, bl, d.y * d.y);
+        two_prod_acc(ah, al, p.x, x.x);
+        two_prod_acc(ah, al, p.y, x.y);
+        two_prod_acc(bh, bl, d.x, d.x);
+        two_prod_acc(bh, bl, d.y, d.y);
     }
     sh[0][threadIdx.x] = ah;
     sh[1][threadIdx.x] = al;
@@ -355,11 +367,13 @@ int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_par
             host_two_sum(bh, bl, h[4 * k + 2]);
             bl += h[4 * k + 3];
         }
-        // 2a - b with the low parts carried along
+        // 2a - b with the low parts carried along; action[0] + action[1] = S
         double sh = 0, sl = 0;
         host_two_sum(sh, sl, 2.0 * ah);
         host_two_sum(sh, sl, -bh);
-        *action = sh + (sl + 2.0 * al - bl);
+        const double lo = sl + 2.0 * al - bl;
+        action[0] = sh + lo;
+        action[1] = lo - (action[0] - sh);
     }
     k_force_N<<<grid_for(g.V, 128), 128, 0, s>>>(g, Spinor64{X, g.lvb}, Spinor64{Y, g.lvb}, N);
     FCUDA(cudaGetLastError());

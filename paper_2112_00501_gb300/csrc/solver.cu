@@ -13,6 +13,7 @@
 // fixed per-thread element order, and a last-block pass that sums the block
 // partials in a fixed order.  Scalars stay on the device; the host reads one
 // residual norm per iteration.
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -1565,8 +1566,10 @@ static_assert(NA_SCAL >= S_TOTAL * sizeof(double), "scalar area too small");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 // device address of the scratch array, looked up once per device (in host
-// code the array's name is only a stand-in, never a device address)
-static void *g_noalloc_base[64];
+// code the array's name is only a stand-in, never a device address).  Atomic,
+// so that two host threads making their first call at once both store the same
+// address instead of racing on a plain pointer.
+static std::atomic<void *> g_noalloc_base[64];
 static double g_noalloc_hscal[2 * MAXM];  // pageable host copy of a few scalars
 
 int solve_noalloc(mgc_clover_s *op, const double *b, double *x, const mgc_solve_params *p, mgc_solve_info *info,
@@ -1583,12 +1586,12 @@ int solve_noalloc(mgc_clover_s *op, const double *b, double *x, const mgc_solve_
     int dev = 0;
     MGC_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(MGC_ERR_INVALID_ARG, "mgc_solve_noalloc: device ordinal above 63");
-    if (!g_noalloc_base[dev]) {
-        void *ptr = nullptr;
+    void *ptr = g_noalloc_base[dev].load(std::memory_order_acquire);
+    if (!ptr) {
         MGC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-        g_noalloc_base[dev] = ptr;
+        g_noalloc_base[dev].store(ptr, std::memory_order_release);
     }
-    unsigned char *base = static_cast<unsigned char *>(g_noalloc_base[dev]);
+    unsigned char *base = static_cast<unsigned char *>(ptr);
     SolverWork W;  // a view of the scratch array: no allocation
     W.m = 4;
     W.lowprec = (p->precond && p->smoother_prec != 64) ? p->smoother_prec : 0;

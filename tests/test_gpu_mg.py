@@ -106,7 +106,11 @@ def test_preconditioner_matches_oracle(smoother):
     got = mg.precond(torch.from_numpy(v).cuda(), n_cy=2, n_jacobi=3, smoother_prec=smoother, coarse_tol=1e-7,
                      coarse_maxit=4000).cpu().numpy()
     want = O.mg_precond(dims, block, agg, -1, KAPPA, U, Cl, Ci, Wo, Dco, v, ncy=2, nj=3, ctol=1e-12, cmaxit=10000)
-    assert rel(got, want) < (1e-4 if smoother == 32 else TOL[16])
+    # the coarse operator here is well conditioned (cond(D_c) ~ 1.1 on this
+    # basis), so the GPU's FP32 coarse solve to 1e-7 moves the result by
+    # ~1e-7: the FP32 bar applies unchanged
+    err = rel(got, want)
+    assert err < TOL[32 if smoother == 32 else 16], err
 
 
 def test_setup_without_adaptive_pass_matches_oracle():

@@ -423,3 +423,24 @@ def test_mr_block_at_equals_mr_block():
         a = O.mr_block(dims, bd, bc, kappa, U, Cl, r, 4)
         b = O.mr_block_at(dims, bd, bc, kappa, csw, U, r, 4)
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tbc", [-1, 1])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_dirac_at_equals_dirac(tbc, dagger):
+    """The sampled operator that checks the full-size Dslash and solves (its
+    clover term built on the fly at each listed site) is the same computation as
+    the pinned whole-lattice D, bit for bit: on every site of a non-cubic
+    lattice, and on a list with repeats, both t boundaries and the x wrap."""
+    dims = (4, 6, 4, 8)
+    kappa, csw = 0.1355, 1.0
+    U = synth.gauge_field(dims, 0.4, 91)
+    Cl = O.clover(dims, kappa, csw, U)
+    psi = synth.gaussian_spinor(dims, 92)
+    V = synth.volume(dims)
+    full = O.dirac(dims, tbc, kappa, U, Cl, psi, dagger=dagger)
+    assert np.array_equal(O.dirac_at(dims, tbc, kappa, csw, U, psi, np.arange(V), dagger=dagger), full)
+    Lx, Ly, Lz, Lt = dims
+    idx = lambda x, y, z, t: x + Lx * (y + Ly * (z + Lz * t))  # noqa: E731
+    sites = [idx(0, 0, 0, 0), idx(Lx - 1, 2, 1, Lt - 1), idx(3, Ly - 1, Lz - 1, 0), idx(1, 1, 1, 3), 7, 7]
+    assert np.array_equal(O.dirac_at(dims, tbc, kappa, csw, U, psi, sites, dagger=dagger), full[sites])
