@@ -10,6 +10,7 @@
 //    over blockIdx.y.
 //  - k_clover_apply: out = C psi or C^-1 psi.
 #include "hop.cuh"
+#include "hop16.cuh"
 #include "mgc_host.h"
 
 namespace mgc {
@@ -220,6 +221,67 @@ __global__ void __launch_bounds__(DIRAC_THREADS, (LVB > 0 && sizeof(typename SPI
     dst.store(i, o);
 }
 
+// ---- the FP16 operator: FP16 links, clover and spinors with their per-site
+// scales, FP32 arithmetic with the FP16 factors fed to the multiply-adds as
+// they are stored (hop16.cuh)
+
+template <bool DAG, int LVB, class GA>
+__global__ void __launch_bounds__(DIRAC_THREADS, 5)
+    k_dirac16(Geom g, Spinor16 in, Spinor16 out, GA U, Clover16 C, float kappa)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int r = blockIdx.y;
+    Spinor16 src = shift_rhs(in, r, g.V), dst = shift_rhs(out, r, g.V);
+    GA Ug = U;
+    Clover16 Cg = C;
+    Geom gg = g;
+    if (LVB > 0) {
+        gg.lvb = LVB;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) gg.lb[mu] = LVB / 4;
+        src.lvb = dst.lvb = Ug.lvb = Cg.lvb = LVB;
+    }
+    int c[4];
+    site_coords(gg, i, c);
+    // C psi (with the clover and spinor scales), then the hops accumulated onto it
+    float ar[12], ai[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ar[k] = ai[k] = 0.f;
+    {
+        uint32_t v[12];
+        words16(src, i, v);
+        clover16_site(Cg, i, v, __ldg(Cg.sc + i) * src.scale_of(i), ar, ai);
+    }
+    hop16_dir<0, DAG>(gg, c, i, src, Ug, -kappa, ar, ai);
+    hop16_dir<1, DAG>(gg, c, i, src, Ug, -kappa, ar, ai);
+    hop16_dir<2, DAG>(gg, c, i, src, Ug, -kappa, ar, ai);
+    hop16_dir<3, DAG>(gg, c, i, src, Ug, -kappa, ar, ai);
+    Cx<float> o[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = Cx<float>{ar[k], ai[k]};
+    dst.store(i, o);
+}
+
+template <int LVB, class GA>
+static void dirac16_launch(const Geom &g, bool dag, Spinor16 in, Spinor16 out, GA U, Clover16 C, double kappa,
+                           int nrhs, cudaStream_t s)
+{
+    dim3 grid(grid_for(g.V, DIRAC_THREADS), nrhs);
+    if (dag) k_dirac16<true, LVB><<<grid, DIRAC_THREADS, 0, s>>>(g, in, out, U, C, (float)kappa);
+    else k_dirac16<false, LVB><<<grid, DIRAC_THREADS, 0, s>>>(g, in, out, U, C, (float)kappa);
+}
+
+template <class GA>
+static void dirac16_dispatch(const Geom &g, bool dag, Spinor16 in, Spinor16 out, GA U, Clover16 C, double kappa,
+                             int nrhs, cudaStream_t s)
+{
+    const bool cube = g.lb[0] == g.lb[1] && g.lb[1] == g.lb[2] && g.lb[2] == g.lb[3];
+    if (cube && g.lvb == 8) dirac16_launch<8>(g, dag, in, out, U, C, kappa, nrhs, s);
+    else if (cube && g.lvb == 4) dirac16_launch<4>(g, dag, in, out, U, C, kappa, nrhs, s);
+    else dirac16_launch<0>(g, dag, in, out, U, C, kappa, nrhs, s);
+}
+
 template <int LVB, class SPI, class SPO, class GA, class CL>
 static void dirac_launch(const Geom &g, bool dag, SPI in, SPO out, GA U, CL C, double kappa, int nrhs, cudaStream_t s)
 {
@@ -262,11 +324,11 @@ int launch_dirac(const mgc_clover_s *op, int prec, bool dag, const void *in, voi
                            nrhs, s);
     } else {
         if (ga->compress == 12)
-            dirac_dispatch(g, dag, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x12{(uint2 *)ga->U16, g.lvb},
-                           cl16(g, op), op->kappa, nrhs, s);
+            dirac16_dispatch(g, dag, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x12{(uint2 *)ga->U16, g.lvb},
+                             cl16(g, op), op->kappa, nrhs, s);
         else
-            dirac_dispatch(g, dag, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x18{(uint32_t *)ga->U16, g.lvb},
-                           cl16(g, op), op->kappa, nrhs, s);
+            dirac16_dispatch(g, dag, sp16(g, in, nrhs), sp16(g, out, nrhs), Gauge16x18{(uint32_t *)ga->U16, g.lvb},
+                             cl16(g, op), op->kappa, nrhs, s);
     }
     MGC_CUDA(cudaGetLastError());
     count(1, (double)g.V * (2.0 * nrhs * spinor_site_bytes(prec) +
