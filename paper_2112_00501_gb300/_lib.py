@@ -81,6 +81,7 @@ SIGNATURES = {
     "mgc_clover_destroy": (_I, [_P]),
     "mgc_device_status": (_I, [_P, C.POINTER(_I), _I, _P]),
     "mgc_selftest_bounded_wait": (_I, [C.c_longlong, _I, C.POINTER(_I), _P]),
+    "mgc_fma_peak": (_I, [_I, C.POINTER(C.c_double), _P]),
     "mgc_clover_export": (_I, [_P, _I, _P, _P]),
     "mgc_apply_D": (_I, [_P, _P, _P, _I, _I, _P]),
     "mgc_apply_Ddag": (_I, [_P, _P, _P, _I, _I, _P]),
@@ -91,7 +92,7 @@ SIGNATURES = {
     "mgc_sap_smooth_A": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P]),
     "mgc_solve_params_default": (None, [C.POINTER(SolveParams)]),
     "mgc_solve": (_I, [_P, _P, _P, _I, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P]),
-    "mgc_force": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(SolveInfo), C.POINTER(_D), _P]),
+    "mgc_force": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P, _P]),
     "mgc_solve_noalloc": (_I, [_P, _P, _P, C.POINTER(SolveParams), C.POINTER(SolveInfo), _P]),
     "mgc_mg_params_default": (None, [C.POINTER(MgParams)]),
     "mgc_mg_create": (_I, [_P, C.POINTER(_I), _I, C.POINTER(_P)]),

@@ -339,6 +339,12 @@ int mgc_selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, voi
     return selftest_bounded_wait(limit_ns, arrive, flag_out, (cudaStream_t)stream);
 }
 
+int mgc_fma_peak(int prec, double *flops_per_s, void *stream)
+{
+    if (!flops_per_s) return fail(MGC_ERR_INVALID_ARG, "NULL argument");
+    return fma_peak(prec, flops_per_s, (cudaStream_t)stream);
+}
+
 int mgc_device_status(mgc_clover_t op, int *flags, int clear, void *stream)
 {
     if (!op || !flags) return fail(MGC_ERR_INVALID_ARG, "NULL argument");

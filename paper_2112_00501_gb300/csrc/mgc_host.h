@@ -121,6 +121,7 @@ int launch_unitarity(const Geom &g, const double *canon_dev, double *d_maxerr, c
 int launch_sap(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_mr,
                int x_is_zero, cudaStream_t s);
 int selftest_bounded_wait(long long limit_ns, int arrive, int *flag_out, cudaStream_t s);
+int fma_peak(int prec, double *flops, cudaStream_t s);
 // the smoother for D with even-odd preconditioned MR domain solves
 int launch_sap_eo(const mgc_clover_s *op, int prec, const void *b, void *x, int nrhs, int n_cy, int n_mr,
                   int x_is_zero, cudaStream_t s);
