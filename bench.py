@@ -36,11 +36,13 @@ WORKLOAD = dict(name="32^3x64", dims=(32, 32, 32, 64), block=(4, 4, 4, 4), eps=0
                 csw=1.0, config_index=2, prec=16, compress=12, n_cy=4, n_mr=4, restart=16, tol=1e-10, inner_tol=2e-6)
 # bounded CPU sample of the same recipe (same eps, kappa, c_sw, solver) at 1/64 of the volume
 CPU_SAMPLE_DIMS = (16, 16, 16, 8)
-FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
-# DRAM bytes (read + write) of one k_sap_h16 colour launch per lattice site,
-# from an ncu capture on 24^3 x 48 (164,292,096 B / 663,552 sites); the
-# kernel's traffic is per domain, so it scales with the sites
-SAP_H16_DRAM_BYTES_PER_SITE = 164292096.0 / 663552
+# derived FP32 FMA peak (SMs x FP32 lanes x 2 x max SM clock), reported beside
+# the rate mgc_fma_peak measures in the run, which is the roofline's peak
+FP32_FMA_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM bytes (read + write) of one k_sap_m16 colour launch per lattice site,
+# from an ncu capture on 24^3 x 48 (155,479,040 + 8,582,656 B over 663,552
+# sites); the kernel's traffic is per domain, so it scales with the sites
+SAP_DRAM_BYTES_PER_SITE = (155479040.0 + 8582656.0) / 663552
 # conventional flop counts per site: hopping 1320, clover 504, kappa axpy 48
 FLOP_D = 1872.0
 
@@ -160,6 +162,85 @@ def oracle_solve_sample(dims, seed_offset=0):
     if st != 0:
         raise RuntimeError("oracle sample did not converge")
     return dt, it, synth.volume(dims), O.threads()
+
+
+def _oracle_sample_fields(dims, seed_offset=0):
+    from paper_2112_00501_gb300 import synth
+
+    w = WORKLOAD
+    U = synth.gauge_field(dims, w["eps"], synth.gauge_seed(w["config_index"]) + 100 + seed_offset)
+    b = synth.gaussian_spinor(dims, synth.source_seed(w["config_index"]) + 100 + seed_offset)
+    return U, b
+
+
+def oracle_legs(dims, threads):
+    """The oracle's D apply, one SAP sweep (4 MR steps per domain, from x = 0)
+    and full solve on a bounded lattice of the workload's recipe, on `threads`
+    threads.  Returns seconds per leg."""
+    from oracle import oracle as O
+
+    w = WORKLOAD
+    U, b = _oracle_sample_fields(dims)
+    n0 = O.threads()
+    O.set_threads(threads)
+    try:
+        Cl = O.clover(dims, w["kappa"], w["csw"], U)
+        t0 = time.perf_counter()
+        O.dirac(dims, -1, w["kappa"], U, Cl, b)
+        t1 = time.perf_counter()
+        O.sap(dims, w["block"], -1, w["kappa"], U, Cl, b, ncy=1, nmr=w["n_mr"])
+        t2 = time.perf_counter()
+        x, st, it, res = O.solve(dims, w["block"], -1, w["kappa"], U, Cl, b, method="fgcr", precond="sap",
+                                 ncy=w["n_cy"], nmr=w["n_mr"], m=w["restart"], tol=w["tol"])
+        t3 = time.perf_counter()
+    finally:
+        O.set_threads(n0)
+    if st != 0:
+        raise RuntimeError("oracle sample did not converge")
+    return {"threads": threads, "d_apply_s": t1 - t0, "sap_sweep_s": t2 - t1, "solve_s": t3 - t2,
+            "solve_outer_iterations": it}
+
+
+def errors_vs_oracle(dims, U, b, d_sites, d_gpu, sap_gpu):
+    """Relative L2 error against the FP64 oracle on the original fields of one
+    D apply (sampled sites) and of one SAP sweep from x = 0 (sampled domains of
+    both colours: a red domain's result is MR_k(D_B, b_B), a black domain's
+    needs its eight red neighbours first), computed site by site."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2112_00501_gb300 import synth
+
+    w = WORKLOAD
+    kappa, csw, block, nmr = w["kappa"], w["csw"], w["block"], w["n_mr"]
+    ref = O.dirac_at(dims, -1, kappa, csw, U, b, d_sites)
+    e_d = float(np.linalg.norm(d_gpu - ref) / np.linalg.norm(ref))
+    nb = [d // q for d, q in zip(dims, block)]
+    doms = [bc for bc in np.ndindex(*nb[::-1])]
+    doms = [tuple(reversed(bc)) for bc in doms]
+    red = [bc for bc in doms if sum(bc) % 2 == 0]
+    black = [bc for bc in doms if sum(bc) % 2 == 1]
+    g = synth.rng(199)
+    got, want = [], []
+    for k in g.choice(len(red), 3, replace=False):
+        sites = O.block_sites(dims, block, red[k])
+        got.append(sap_gpu(sites))
+        want.append(O.mr_block_at(dims, block, red[k], kappa, csw, U, b[sites], nmr))
+    for k in g.choice(len(black), 2, replace=False):
+        bc = black[k]
+        x = np.zeros_like(b)
+        for mu in range(4):
+            for d in (-1, 1):
+                nbc = list(bc)
+                nbc[mu] = (nbc[mu] + d) % nb[mu]
+                s = O.block_sites(dims, block, nbc)
+                x[s] = O.mr_block_at(dims, block, nbc, kappa, csw, U, b[s], nmr)
+        sites = O.block_sites(dims, block, bc)
+        r = b[sites] - O.dirac_at(dims, -1, kappa, csw, U, x, sites)
+        got.append(sap_gpu(sites))
+        want.append(O.mr_block_at(dims, block, bc, kappa, csw, U, r, nmr))
+    a, c = np.concatenate(got), np.concatenate(want)
+    return e_d, float(np.linalg.norm(a - c) / np.linalg.norm(c))
 
 
 def run_reference(args, rank, world):
@@ -607,13 +688,17 @@ def main():
         op.solve(b_pin, params, out=x_pin)
         barrier()
         counters(lib, reset=True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e_ms = []
         for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
             xh, info_e = op.solve(b_pin, params, out=x_pin)
-        e1.record(stream)
+            e1.record(stream)
+            e1.synchronize()
+            e_ms.append(e0.elapsed_time(e1))
         barrier()
-        t_e2e = e0.elapsed_time(e1) / 1e3
+        # the median step: host transfers vary from process to process
+        t_e2e = statistics.median(e_ms) * args.steps / 1e3
         _, nbytes_e2e = counters(lib, reset=True)
 
     # ---------------- the dominant kernel: SAP colour launches, timed alone
@@ -645,6 +730,21 @@ def main():
     n_x0 = 1  # launches per call with x == 0
     flops_call = 0.5 * V * (launches_per_call * w["n_mr"] * flop_mr + (launches_per_call - n_x0) * flop_res)
     sap_tflops = flops_call / (statistics.median(sap_ms) / 1e3) / 1e12
+
+    # ---------------- measured FMA rates (the roofline's peak for the arithmetic-bound kernels)
+    f32_peak, f64_peak = C.c_double(0), C.c_double(0)
+    if lib.mgc_fma_peak(32, C.byref(f32_peak), C.c_void_p(stream.cuda_stream)) != 0 or \
+            lib.mgc_fma_peak(64, C.byref(f64_peak), C.c_void_p(stream.cuda_stream)) != 0:
+        raise RuntimeError("mgc_fma_peak failed: " + lib.mgc_last_error().decode())
+    fp32_peak_tflops, fp64_peak_tflops = f32_peak.value / 1e12, f64_peak.value / 1e12
+    counters(lib, reset=True)
+
+    # ---------------- results for the error against the FP64 oracle (CPU leg)
+    d_sites = synth.rng(77).choice(V, 2048, replace=False)
+    d_sites = np.concatenate([d_sites, [0, V - 1]])
+    d_gpu = op.D(b, prec=w["prec"]).cpu().numpy()[d_sites]
+    sap_full = op.sap(b, prec=w["prec"], n_cy=1, n_mr=w["n_mr"]).cpu().numpy()
+    counters(lib, reset=True)
 
     # ---------------- Dslash alone (workload storage and FP64)
     def time_dslash(prec, dop=op):
@@ -690,6 +790,29 @@ def main():
         f1.synchronize()
         fp64 = {"ms": f0.elapsed_time(f1), "iters": i64.iters, "true_res": i64.true_res}
         del op64, g64
+    counters(lib, reset=True)
+
+    # ---------------- FP64 FGCR (FP64 vectors, inner products and orthogonalisation)
+    # around the FP16 smoother: the benchmark definition's precision pattern
+    # taken literally, beside the default two-level solve
+    fgcr16 = None
+    if not args.no_fp64_path:
+        pf = api.solve_params(method=0, precond=1, smoother_prec=w["prec"], n_cy=w["n_cy"], n_mr=w["n_mr"],
+                              restart=w["restart"], tol=w["tol"], max_iter=500)
+        xf, inf = op.solve(b, pf)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        nf = 3
+        for _ in range(nf):
+            xf, inf = op.solve(b, pf)
+            if inf.status != 0 or inf.true_res > w["tol"]:
+                raise RuntimeError(f"FGCR solve failed: status {inf.status}, residual {inf.true_res}")
+        g1.record(stream)
+        g1.synchronize()
+        fgcr16 = {"method": "FGCR(16) with FP64 vectors, inner products and orthogonalisation, FP64 operator, "
+                            "preconditioned by the FP16-storage smoother",
+                  "ms": g0.elapsed_time(g1) / nf, "iters": inf.iters, "true_res": inf.true_res}
     counters(lib, reset=True)
 
     # ---------------- the paper's own QWS solve (method 3) on the same system
@@ -798,7 +921,10 @@ def main():
         "true_residual": true_res,
         "fp64_path": fp64,
         "mixed_over_fp64_speedup": (fp64["ms"] / (1e3 * t_max / args.steps)) if fp64 else None,
+        "fgcr_fp64_fp16_smoother": fgcr16,
         "dslash": {"fp16_12real_gbs": by_d16 / t_d16 / 1e9, "fp16_us": 1e6 * t_d16,
+                   "fp64_tflops": FLOP_D * V / t_d64 / 1e12,
+                   "fp64_frac_fp64_peak": FLOP_D * V / t_d64 / 1e12 / fp64_peak_tflops,
                    "fp32_12real_gbs": by_d32 / t_d32 / 1e9, "fp32_us": 1e6 * t_d32,
                    "fp32_frac_hbm": (by_d32 / t_d32 / 1e9 / hbm) if hbm else None,
                    "fp64_gbs": by_d64 / t_d64 / 1e9, "fp64_us": 1e6 * t_d64,
@@ -807,25 +933,32 @@ def main():
                    "fp16_18real_frac_hbm": (by_d16_18 / t_d16_18 / 1e9 / hbm) if hbm else None},
         "sap_sweep": {"launch_us": 1e6 * t_launch, "algorithmic_gbs": bytes_launch / t_launch / 1e9,
                       "frac_hbm": (bytes_launch / t_launch / 1e9 / hbm) if hbm else None,
-                      "tflops_fp32": sap_tflops, "frac_fp32_peak": sap_tflops / FP32_FMA_PEAK_TFLOPS},
+                      "tflops_fp32": sap_tflops, "frac_fp32_peak": sap_tflops / fp32_peak_tflops,
+                      "frac_fp32_peak_derived": sap_tflops / FP32_FMA_PEAK_DERIVED_TFLOPS},
+        "fma_peaks": {"fp32_tflops": fp32_peak_tflops, "fp64_tflops": fp64_peak_tflops,
+                      "fp32_derived_tflops": FP32_FMA_PEAK_DERIVED_TFLOPS,
+                      "source": "mgc_fma_peak in this run: 8 independent FMA chains per thread, "
+                                "eight 256-thread blocks per SM, fastest of five launches"},
         "roofline": {
-            "kernel": "k_sap_h16 (FP16 storage, 12-real links, 4^4 domains, 4 MR steps)",
+            "kernel": "k_sap_m16 (SAP colour launch, FP16 storage, 12-real links, 4^4 domains, 4 MR steps)",
             "bound": "alu",
             "achieved": sap_tflops,
-            "peak": FP32_FMA_PEAK_TFLOPS,
+            "peak": fp32_peak_tflops,
             "unit": "TFLOP/s",
-            "frac": sap_tflops / FP32_FMA_PEAK_TFLOPS,
-            "traffic": SAP_H16_DRAM_BYTES_PER_SITE * V,
+            "frac": sap_tflops / fp32_peak_tflops,
+            "traffic": SAP_DRAM_BYTES_PER_SITE * V if SAP_DRAM_BYTES_PER_SITE else None,
             "algorithmic_bytes": bytes_launch,
             "algorithmic_gbs": bytes_launch / t_launch / 1e9,
             "frac_hbm": (bytes_launch / t_launch / 1e9 / hbm) if hbm else None,
-            "peak_source": "FP32 FMA peak from unit counts and clock: 152 SMs x 128 lanes x 2 flop x 2.070 GHz; "
-                           "HBM fraction against MEASURED_PEAKS.json hbm_gbs (measured)",
+            "peak_source": "FP32 FMA rate measured in this run (mgc_fma_peak, of measured); HBM fraction "
+                           "against MEASURED_PEAKS.json hbm_gbs (of measured)",
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 24^3x48, "
                               "scaled by sites",
         },
         "e2e": {"value": nbytes_e2e / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": V * 192,
-                "d2h_bytes_per_step": V * 192, "ms_per_step": 1e3 * t_e2e / args.steps},
+                "d2h_bytes_per_step": V * 192, "ms_per_step": 1e3 * t_e2e / args.steps,
+                "ms_steps": e_ms if not args.no_e2e else None,
+                "timing": "median of the per-step times (each step bracketed by its own events) x steps"},
         "bytes_per_site_iteration": bytes_per_site_iter,
         "qws_solve": qws,
         "multigrid": mgres,
@@ -834,14 +967,30 @@ def main():
         "c1": c1,
     }
     if not args.no_cpu_baseline:
-        dt, it, Vs, thr = oracle_solve_sample(CPU_SAMPLE_DIMS)
-        cpu_val = bytes_per_site_iter * it * Vs / dt / 1e9
+        # the CPU leg: the FP64 oracle timed on the host cores (one thread and
+        # all cores of this process's affinity), and the error of the timed
+        # storage format's results against it
+        ncores = len(os.sched_getaffinity(0))
+        legs = [oracle_legs(CPU_SAMPLE_DIMS, 1), oracle_legs(CPU_SAMPLE_DIMS, ncores)]
+        Vs = 1
+        for d in CPU_SAMPLE_DIMS:
+            Vs *= d
+        it = legs[1]["solve_outer_iterations"]
+        cpu_val = bytes_per_site_iter * it * Vs / legs[1]["solve_s"] / 1e9
         line["cpu_baseline"] = {
-            "value": cpu_val, "unit": "GB/s", "cores": thr, "kind": "oracle",
-            "sample": f"FP64 oracle FGCR+SAP solve to 1e-10 of the same recipe on "
-                      f"{'x'.join(map(str, CPU_SAMPLE_DIMS))} ({Vs} sites, {it} outer iterations, "
-                      f"{dt:.1f} s); GB/s = this run's algorithmic bytes per site-iteration "
-                      f"({bytes_per_site_iter:.0f} B) x site-iterations/s"}
+            "value": cpu_val, "unit": "GB/s", "cores": ncores, "kind": "oracle",
+            "sample": f"FP64 oracle on {'x'.join(map(str, CPU_SAMPLE_DIMS))} ({Vs} sites) of the same recipe: "
+                      f"D apply, one SAP sweep (4 MR steps per domain) and the FGCR+SAP solve to 1e-10 "
+                      f"({it} outer iterations), on 1 thread and on {ncores}; value = the {ncores}-thread "
+                      f"solve as this run's algorithmic bytes per site-iteration ({bytes_per_site_iter:.0f} B) x "
+                      f"site-iterations/s",
+            "legs": legs}
+        e_d, e_s = errors_vs_oracle(dims, U, b_host, d_sites, d_gpu, lambda sites: sap_full[sites])
+        line["error_vs_oracle"] = {
+            "dslash": e_d, "sap_sweep": e_s, "tolerance": 2e-3,
+            "what": "relative L2 error against the FP64 oracle on the original fields, at the timed storage "
+                    "(FP16 + per-site scale, 12-real links): D on 2050 sampled sites of 32^3x64; one SAP sweep "
+                    "from x = 0 (4 MR steps) on 3 red and 2 black sampled domains"}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -27,6 +27,7 @@
 // form e_o = C_oo^-1 (r_o + kappa H_oe e_e).  Odd entries of the shared vector
 // hold the odd-site intermediate, even entries the even-site residual.
 #include "hop.cuh"
+#include "hop16.cuh"
 #include "mgc_host.h"
 #include "tma.cuh"
 
@@ -1036,13 +1037,255 @@ __device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, c
     xx.store(i, e);
 }
 
+// ---- the FP16 smoother's MR domain solve with FP16-operand arithmetic
+// (hop16.cuh): the staged links and clover words and an FP16 copy of r (one
+// FP32 scale per site, the storage convention of the FP16 fields) are the
+// factors of D_B r, fed to the FP32 multiply-adds as stored.  r itself, e and
+// p stay in FP32 registers: the inner products, alpha and the updates are the
+// FP32 arithmetic of the MR step, and only the operator sees r rounded to
+// FP16, as it sees every FP16-stored spinor.  Shared memory as in k_sap_h16,
+// the r area holding the FP16 copy of r and its scales.
+
+template <int MU, int SGN, int VB>
+__device__ __forceinline__ void m16_hop(const uint4 *r16, const float *rsc, int n, const uint32_t *sL, int lk, float mk,
+                                        float ar[12], float ai[12])
+{
+    uint32_t s[12], h[6], u[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const uint4 v = r16[k * VB + n];
+        s[4 * k] = v.x;
+        s[4 * k + 1] = v.y;
+        s[4 * k + 2] = v.z;
+        s[4 * k + 3] = v.w;
+    }
+    const float coef = mk * rsc[n];
+    project16<MU, SGN>(s, h);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = sL[(MU * 9 + k) * VB + lk];
+    float wr[6], wi[6];
+    su3_mul16<(SGN > 0)>(u, h, wr, wi);
+    reconstruct16<MU, SGN>(ar, ai, wr, wi, coef);
+}
+
+// r (FP32) to its FP16 copy at local site l: the site's largest |component| as
+// the scale, components divided by it and rounded to nearest
+template <int VB>
+__device__ __forceinline__ void m16_store_r(uint4 *r16, float *rsc, int l, const float rr[12], const float ri[12])
+{
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(rr[k]), fabsf(ri[k])));
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        r16[k * VB + l] = make_uint4(pack_half2(rr[4 * k] * inv, ri[4 * k] * inv),
+                                     pack_half2(rr[4 * k + 1] * inv, ri[4 * k + 1] * inv),
+                                     pack_half2(rr[4 * k + 2] * inv, ri[4 * k + 2] * inv),
+                                     pack_half2(rr[4 * k + 3] * inv, ri[4 * k + 3] * inv));
+    rsc[l] = m;
+}
+
+template <int LVB, class GA>
+__device__ __forceinline__ void sap_m16_body(const Geom &g, const Spinor16 &b, const Spinor16 &x, const GA &U,
+                                             const Clover16 &C, float kappa, int colour, int nmr, int x_zero,
+                                             int *status, int jb, int rr)
+{
+    constexpr int VB = 1 << LVB;
+    constexpr int LB = LVB / 4;
+    using HL = H16Links<GA>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint32_t *sL = reinterpret_cast<uint32_t *>(smem);     // [4][9][VB] half2
+    uint4 *sC = reinterpret_cast<uint4 *>(sL + 36 * VB);   // [9][VB]
+    float *sS = reinterpret_cast<float *>(sC + 9 * VB);    // [VB]
+    uint4 *area = reinterpret_cast<uint4 *>(sS + VB);      // 96 VB bytes: 12-real link stage, then r
+    uint4 *r16 = area;                                     // [3][VB] FP16 copy of r
+    float *rsc = reinterpret_cast<float *>(area + 3 * VB); // [VB] its scales
+    float *red = reinterpret_cast<float *>(area + 6 * VB); // 96 floats
+    uint64_t *bar = reinterpret_cast<uint64_t *>(red + 96);
+    static_assert(HL::STAGE * VB % 16 == 0 && 144 * VB % 16 == 0 && 4 * VB % 16 == 0,
+                  "bulk copies move multiples of 16 bytes");
+    static_assert(52 * VB <= 96 * VB, "the FP16 copy of r fits the stage area");
+
+    Geom gg = g;
+    gg.lvb = LVB;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) gg.lb[mu] = LB;
+    Spinor16 bb = shift_rhs(b, rr, g.V), xx = shift_rhs(x, rr, g.V);
+    bb.lvb = LVB;
+    xx.lvb = LVB;
+    GA Ug = U;
+    Ug.lvb = LVB;
+    int j = jb;
+    const int half0 = g.NB[0] >> 1;
+    int bc[4];
+    const int m = j % half0;
+    j /= half0;
+    bc[1] = j % g.NB[1];
+    j /= g.NB[1];
+    bc[2] = j % g.NB[2];
+    bc[3] = j / g.NB[2];
+    bc[0] = 2 * m + ((colour + bc[1] + bc[2] + bc[3]) & 1);
+    const int blk = block_index(gg, bc);
+    const int l = threadIdx.x;
+    const int i = (blk << LVB) | l;
+
+    if (l == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (l == 0) {
+        const unsigned lbytes = HL::STAGE * VB, cb = 144 * VB, sb = 4 * VB;
+        mbar_arrive_expect_tx(bar, lbytes + cb + sb);
+        bulk_g2s(HL::EXPAND ? (void *)area : (void *)sL, HL::src(U, blk, LVB), lbytes, bar);
+        bulk_g2s(sC, C.p + ((size_t)blk * 9 << LVB), cb, bar);
+        bulk_g2s(sS, C.sc + ((size_t)blk << LVB), sb, bar);
+    }
+
+    int lc[4], cg[4];
+    local_coords(gg, l, lc);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) cg[mu] = (bc[mu] << LB) + lc[mu];
+
+    // 1. hopping part of D x from global memory while the copies land
+    float ar[12], ai[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ar[k] = ai[k] = 0.f;
+    if (!x_zero) {
+        hop16_dir<0, false>(gg, cg, i, xx, Ug, -kappa, ar, ai);
+        hop16_dir<1, false>(gg, cg, i, xx, Ug, -kappa, ar, ai);
+        hop16_dir<2, false>(gg, cg, i, xx, Ug, -kappa, ar, ai);
+        hop16_dir<3, false>(gg, cg, i, xx, Ug, -kappa, ar, ai);
+    }
+
+    const bool ok = mbar_wait_bounded(bar, 0, WAIT_LIMIT_NS);
+    if (!__syncthreads_and(ok)) {
+        mbar_wait_bounded(bar, 0, WAIT_LIMIT_NS);
+        if (l == 0) atomicOr(status, MGC_DEV_TIMEOUT);
+        return;
+    }
+    if (HL::EXPAND) {
+        // rows 0 and 1 staged in the r area; row 2 = conj(row0 x row1) once per link
+        const uint2 *st = reinterpret_cast<const uint2 *>(area);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            uint32_t u[9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint2 v = st[(mu * 3 + k) * VB + l];
+                u[2 * k] = v.x;
+                u[2 * k + 1] = v.y;
+            }
+            row2_16(u);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sL[(mu * 9 + k) * VB + l] = u[k];
+        }
+        __syncthreads();  // links complete, r area free
+    }
+
+    // r_B = b - (C x - kappa H x)
+    float rvr[12], rvi[12];
+    {
+        Cx<float> bv[12];
+        bb.load(i, bv);
+        if (!x_zero) {
+            uint32_t v[12];
+            words16(xx, i, v);
+            clover_planes16<false>(sC + l, VB, v, sS[l] * xx.scale_of(i), ar, ai);
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            rvr[k] = bv[k].r - ar[k];
+            rvi[k] = bv[k].i - ai[k];
+        }
+    }
+    int nf[4], nb[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        int t[4] = {lc[0], lc[1], lc[2], lc[3]};
+        t[mu] = lc[mu] + 1;
+        nf[mu] = (t[mu] < (1 << LB)) ? local_index(gg, t) : -1;
+        t[mu] = lc[mu] - 1;
+        nb[mu] = (t[mu] >= 0) ? local_index(gg, t) : -1;
+    }
+    m16_store_r<VB>(r16, rsc, l, rvr, rvi);
+    float er[12], ei[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) er[k] = ei[k] = 0.f;
+    __syncthreads();
+
+    // 2. minimal residual on D_B: p = D_B r (r's FP16 copy), alpha = <p, r>/<p, p>,
+    // e += alpha r, r -= alpha p
+    for (int it = 0; it < nmr; ++it) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ar[k] = ai[k] = 0.f;
+        {
+            uint32_t v[12];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint4 w = r16[k * VB + l];
+                v[4 * k] = w.x;
+                v[4 * k + 1] = w.y;
+                v[4 * k + 2] = w.z;
+                v[4 * k + 3] = w.w;
+            }
+            clover_planes16<false>(sC + l, VB, v, sS[l] * rsc[l], ar, ai);
+        }
+        const float mk = -kappa;
+        if (nf[0] >= 0) m16_hop<0, -1, VB>(r16, rsc, nf[0], sL, l, mk, ar, ai);
+        if (nb[0] >= 0) m16_hop<0, +1, VB>(r16, rsc, nb[0], sL, nb[0], mk, ar, ai);
+        if (nf[1] >= 0) m16_hop<1, -1, VB>(r16, rsc, nf[1], sL, l, mk, ar, ai);
+        if (nb[1] >= 0) m16_hop<1, +1, VB>(r16, rsc, nb[1], sL, nb[1], mk, ar, ai);
+        if (nf[2] >= 0) m16_hop<2, -1, VB>(r16, rsc, nf[2], sL, l, mk, ar, ai);
+        if (nb[2] >= 0) m16_hop<2, +1, VB>(r16, rsc, nb[2], sL, nb[2], mk, ar, ai);
+        if (nf[3] >= 0) m16_hop<3, -1, VB>(r16, rsc, nf[3], sL, l, mk, ar, ai);
+        if (nb[3] >= 0) m16_hop<3, +1, VB>(r16, rsc, nb[3], sL, nb[3], mk, ar, ai);
+        float pr = 0.f, pi = 0.f, pp = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            pr = fmaf(ar[k], rvr[k], fmaf(ai[k], rvi[k], pr));
+            pi = fmaf(ar[k], rvi[k], fmaf(-ai[k], rvr[k], pi));
+            pp = fmaf(ar[k], ar[k], fmaf(ai[k], ai[k], pp));
+        }
+        block_sum3(pr, pi, pp, red);
+        const float alr = pp > 0.f ? pr / pp : 0.f, ali = pp > 0.f ? pi / pp : 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            er[k] = fmaf(alr, rvr[k], fmaf(-ali, rvi[k], er[k]));
+            ei[k] = fmaf(alr, rvi[k], fmaf(ali, rvr[k], ei[k]));
+            rvr[k] = fmaf(-alr, ar[k], fmaf(ali, ai[k], rvr[k]));
+            rvi[k] = fmaf(-alr, ai[k], fmaf(-ali, ar[k], rvi[k]));
+        }
+        m16_store_r<VB>(r16, rsc, l, rvr, rvi);
+        __syncthreads();
+    }
+
+    // 3. x_B += e
+    Cx<float> eo[12];
+    if (!x_zero) {
+        Cx<float> xo[12];
+        xx.load(i, xo);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) eo[k] = Cx<float>{er[k] + xo[k].r, ei[k] + xo[k].i};
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) eo[k] = Cx<float>{er[k], ei[k]};
+    }
+    xx.store(i, eo);
+}
+
+template <int LVB, class GA>
+__global__ void __launch_bounds__(1 << LVB, 2) k_sap_m16(Geom g, Spinor16 b, Spinor16 x, GA U, Clover16 C, float kappa,
+                                                         int colour, int nmr, int x_zero, int *status)
+{
+    sap_m16_body<LVB>(g, b, x, U, C, kappa, colour, nmr, x_zero, status, blockIdx.x, blockIdx.y);
+}
+
 template <bool JAC, int LVB, class GA>
 static int sap_run_h16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clover16 C, int nrhs, int n_cy, int n_mr,
                        int x_is_zero, cudaStream_t s, int compress)
 {
     const Geom &g = op->gauge->lat->g;
     constexpr size_t smem = h16_smem_bytes<LVB>();
-    auto kern = k_sap_h16<JAC, LVB, GA>;
+    auto kern = JAC ? k_sap_h16<JAC, LVB, GA> : k_sap_m16<LVB, GA>;
     MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(g.nblocks / 2, nrhs);
     for (int cy = 0; cy < n_cy; ++cy)
@@ -1388,7 +1631,7 @@ __global__ void __launch_bounds__(1 << LVB, 2) k_sap_h16_batch(SapBatch<Spinor16
 {
     int k, jb, rr;
     batch_item(B, k, jb, rr);
-    sap_h16_body<false, LVB>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
+    sap_m16_body<LVB>(B.g[k], B.b[k], B.x[k], B.U[k], B.C[k], B.kappa[k], colour, nmr, x_zero, B.status[k], jb, rr);
 }
 
 template <int LVB, class GA>
