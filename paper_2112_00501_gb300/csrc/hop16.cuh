@@ -9,11 +9,8 @@
 // once per hop as the real coefficient of the FP32 accumulation.
 //
 // A complex number is one 32-bit word: the real part in the low half, the
-// imaginary part in the high half.  Complex products use a second word per
-// vector entry, i*h = (-Im h, Re h) (or -i*h for the conjugated link), so that
-// every real product is one FMA with no negation:
-//   (u h).re = u.re h.re + u.im (i h).re,   (u h).im = u.re h.im + u.im (i h).im
-//   (u* h).re = u.re h.re + u.im (-i h).re, (u* h).im = u.re h.im + u.im (-i h).im
+// imaginary part in the high half; a complex product is four FMAs on the
+// halves.
 //
 // The spin projection of the hopping term (Eq. (1)) is formed on the packed
 // halves (one FP16 addition per component), so the projected half spinor, the
@@ -27,21 +24,48 @@
 
 namespace mgc {
 
-__device__ __forceinline__ unsigned short h_lo(uint32_t w) { return (unsigned short)(w & 0xffffu); }
-__device__ __forceinline__ unsigned short h_hi(uint32_t w) { return (unsigned short)(w >> 16); }
+// The products below split each 32-bit word into its halves inside one asm
+// block (mov.b32 {lo, hi}), which addresses the halves in place, and negate a
+// factor there (folded into the multiply-add): no instruction is spent on
+// extracting, swapping or negating halves.
 
-// a * b + c with FP16 factors and FP32 addend and result
-__device__ __forceinline__ float mfma(unsigned short a, unsigned short b, float c)
+// acc += u * h:  re += u.re h.re - u.im h.im,  im += u.re h.im + u.im h.re
+__device__ __forceinline__ void cmac16(float &ar, float &ai, uint32_t u, uint32_t h)
 {
-    float d;
-    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
-    return d;
+    asm("{\n\t.reg .f16 u0, u1, h0, h1, n1;\n\t"
+        "mov.b32 {u0, u1}, %2;\n\tmov.b32 {h0, h1}, %3;\n\tneg.f16 n1, u1;\n\t"
+        "fma.rn.f32.f16 %0, u0, h0, %0;\n\tfma.rn.f32.f16 %1, u0, h1, %1;\n\t"
+        "fma.rn.f32.f16 %0, n1, h1, %0;\n\tfma.rn.f32.f16 %1, u1, h0, %1;\n\t}"
+        : "+f"(ar), "+f"(ai)
+        : "r"(u), "r"(h));
 }
-
-// i * z and -i * z of a packed complex half pair
-__device__ __forceinline__ uint32_t h2_times_i(uint32_t z) { return __byte_perm(z, 0, 0x1032) ^ 0x00008000u; }
-__device__ __forceinline__ uint32_t h2_times_mi(uint32_t z) { return __byte_perm(z, 0, 0x1032) ^ 0x80000000u; }
-__device__ __forceinline__ uint32_t h2_neg(uint32_t z) { return z ^ 0x80008000u; }
+// acc += conj(u) * h:  re += u.re h.re + u.im h.im,  im += u.re h.im - u.im h.re
+__device__ __forceinline__ void cjmac16(float &ar, float &ai, uint32_t u, uint32_t h)
+{
+    asm("{\n\t.reg .f16 u0, u1, h0, h1, n1;\n\t"
+        "mov.b32 {u0, u1}, %2;\n\tmov.b32 {h0, h1}, %3;\n\tneg.f16 n1, u1;\n\t"
+        "fma.rn.f32.f16 %0, u0, h0, %0;\n\tfma.rn.f32.f16 %1, u0, h1, %1;\n\t"
+        "fma.rn.f32.f16 %0, u1, h1, %0;\n\tfma.rn.f32.f16 %1, n1, h0, %1;\n\t}"
+        : "+f"(ar), "+f"(ai)
+        : "r"(u), "r"(h));
+}
+// (re, im) = d * x for the real half d (the high half of dw when HI, else the low)
+template <bool HI>
+__device__ __forceinline__ void rmul16(float &re, float &im, uint32_t dw, uint32_t x)
+{
+    if (HI)
+        asm("{\n\t.reg .f16 d0, d1, x0, x1;\n\t"
+            "mov.b32 {d0, d1}, %2;\n\tmov.b32 {x0, x1}, %3;\n\t"
+            "fma.rn.f32.f16 %0, d1, x0, 0f00000000;\n\tfma.rn.f32.f16 %1, d1, x1, 0f00000000;\n\t}"
+            : "=f"(re), "=f"(im)
+            : "r"(dw), "r"(x));
+    else
+        asm("{\n\t.reg .f16 d0, d1, x0, x1;\n\t"
+            "mov.b32 {d0, d1}, %2;\n\tmov.b32 {x0, x1}, %3;\n\t"
+            "fma.rn.f32.f16 %0, d0, x0, 0f00000000;\n\tfma.rn.f32.f16 %1, d0, x1, 0f00000000;\n\t}"
+            : "=f"(re), "=f"(im)
+            : "r"(dw), "r"(x));
+}
 
 __device__ __forceinline__ uint32_t h2_add(uint32_t a, uint32_t b)
 {
@@ -54,20 +78,26 @@ __device__ __forceinline__ uint32_t h2_sub(uint32_t a, uint32_t b)
     return *reinterpret_cast<uint32_t *>(&r);
 }
 
-// acc += u * h (iu = i*h), acc += conj(u) * h (nih = -i*h)
-__device__ __forceinline__ void cmac16(float &ar, float &ai, uint32_t u, uint32_t h, uint32_t ih)
+// z + i w and z - i w on packed halves: w's halves swapped and scaled by
+// (-1, 1) or (1, -1) in one FP16x2 multiply-add (the factors are exact, so the
+// result is z + (-Im w, Re w), or z + (Im w, -Re w), rounded once)
+__device__ __forceinline__ uint32_t h2_add_iw(uint32_t z, uint32_t w)
 {
-    ar = mfma(h_lo(u), h_lo(h), ar);
-    ai = mfma(h_lo(u), h_hi(h), ai);
-    ar = mfma(h_hi(u), h_lo(ih), ar);
-    ai = mfma(h_hi(u), h_hi(ih), ai);
+    uint32_t d;
+    asm("{\n\t.reg .b16 w0, w1;\n\t.reg .b32 sw;\n\t"
+        "mov.b32 {w0, w1}, %2;\n\tmov.b32 sw, {w1, w0};\n\tfma.rn.f16x2 %0, sw, %3, %1;\n\t}"
+        : "=r"(d)
+        : "r"(z), "r"(w), "r"(0x3C00BC00u));
+    return d;
 }
-__device__ __forceinline__ void cjmac16(float &ar, float &ai, uint32_t u, uint32_t h, uint32_t nih)
+__device__ __forceinline__ uint32_t h2_sub_iw(uint32_t z, uint32_t w)
 {
-    ar = mfma(h_lo(u), h_lo(h), ar);
-    ai = mfma(h_lo(u), h_hi(h), ai);
-    ar = mfma(h_hi(u), h_lo(nih), ar);
-    ai = mfma(h_hi(u), h_hi(nih), ai);
+    uint32_t d;
+    asm("{\n\t.reg .b16 w0, w1;\n\t.reg .b32 sw;\n\t"
+        "mov.b32 {w0, w1}, %2;\n\tmov.b32 sw, {w1, w0};\n\tfma.rn.f16x2 %0, sw, %3, %1;\n\t}"
+        : "=r"(d)
+        : "r"(z), "r"(w), "r"(0xBC003C00u));
+    return d;
 }
 
 // Spin projection (1 + SGN gamma_mu) psi on packed halves, psi[spin*3 + colour]:
@@ -79,13 +109,22 @@ __device__ __forceinline__ void project16(const uint32_t s[12], uint32_t h[6])
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const uint32_t a = s[6 + c], b = s[9 + c];
-        uint32_t o0, o1;  // i s_k (a, b), or (a, b) in time
-        if (MU == 0) { o0 = h2_times_i(b); o1 = h2_times_i(a); }
-        if (MU == 1) { o0 = b; o1 = h2_neg(a); }
-        if (MU == 2) { o0 = h2_times_i(a); o1 = h2_times_mi(b); }
-        if (MU == 3) { o0 = a; o1 = b; }
-        if (SGN > 0) { h[c] = h2_sub(s[c], o0); h[3 + c] = h2_sub(s[3 + c], o1); }
-        else { h[c] = h2_add(s[c], o0); h[3 + c] = h2_add(s[3 + c], o1); }
+        if (MU == 0) {
+            h[c] = SGN > 0 ? h2_sub_iw(s[c], b) : h2_add_iw(s[c], b);
+            h[3 + c] = SGN > 0 ? h2_sub_iw(s[3 + c], a) : h2_add_iw(s[3 + c], a);
+        }
+        if (MU == 1) {
+            h[c] = SGN > 0 ? h2_sub(s[c], b) : h2_add(s[c], b);
+            h[3 + c] = SGN > 0 ? h2_add(s[3 + c], a) : h2_sub(s[3 + c], a);
+        }
+        if (MU == 2) {
+            h[c] = SGN > 0 ? h2_sub_iw(s[c], a) : h2_add_iw(s[c], a);
+            h[3 + c] = SGN > 0 ? h2_add_iw(s[3 + c], b) : h2_sub_iw(s[3 + c], b);
+        }
+        if (MU == 3) {
+            h[c] = SGN > 0 ? h2_sub(s[c], a) : h2_add(s[c], a);
+            h[3 + c] = SGN > 0 ? h2_sub(s[3 + c], b) : h2_add(s[3 + c], b);
+        }
     }
 }
 
@@ -94,9 +133,6 @@ __device__ __forceinline__ void project16(const uint32_t s[12], uint32_t h[6])
 template <bool DAG>
 __device__ __forceinline__ void su3_mul16(const uint32_t u[9], const uint32_t h[6], float wr[6], float wi[6])
 {
-    uint32_t ih[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) ih[k] = DAG ? h2_times_mi(h[k]) : h2_times_i(h[k]);
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -104,8 +140,8 @@ __device__ __forceinline__ void su3_mul16(const uint32_t u[9], const uint32_t h[
             float ar = 0.f, ai = 0.f;
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                if (DAG) cjmac16(ar, ai, u[b * 3 + a], h[3 * s + b], ih[3 * s + b]);
-                else cmac16(ar, ai, u[a * 3 + b], h[3 * s + b], ih[3 * s + b]);
+                if (DAG) cjmac16(ar, ai, u[b * 3 + a], h[3 * s + b]);
+                else cmac16(ar, ai, u[a * 3 + b], h[3 * s + b]);
             }
             wr[3 * s + a] = ar;
             wi[3 * s + a] = ai;
@@ -117,24 +153,24 @@ __device__ __forceinline__ void su3_mul16(const uint32_t u[9], const uint32_t h[
 // in which an uncompressed FP16 link stores it)
 __device__ __forceinline__ void row2_16(uint32_t u[9])
 {
-    const uint32_t n0 = h2_neg(u[0]), n1 = h2_neg(u[1]), n2 = h2_neg(u[2]);
-    const uint32_t i3 = h2_times_i(u[3]), i4 = h2_times_i(u[4]), i5 = h2_times_i(u[5]);
-    // conj(a b - c d) = (a b - c d).re - i (a b - c d).im
-    auto entry = [](uint32_t a, uint32_t na, uint32_t b, uint32_t ib, uint32_t c, uint32_t nc, uint32_t d,
-                    uint32_t id) {
-        float re = mfma(h_lo(a), h_lo(b), 0.f);
-        re = mfma(h_hi(a), h_lo(ib), re);
-        re = mfma(h_lo(nc), h_lo(d), re);
-        re = mfma(h_hi(nc), h_lo(id), re);
-        float im = mfma(h_lo(na), h_hi(b), 0.f);  // -(a b).im + (c d).im
-        im = mfma(h_hi(na), h_hi(ib), im);
-        im = mfma(h_lo(c), h_hi(d), im);
-        im = mfma(h_hi(c), h_hi(id), im);
+    // conj(a b - c d):  re = a.re b.re - a.im b.im - c.re d.re + c.im d.im,
+    //                   im = -a.re b.im - a.im b.re + c.re d.im + c.im d.re
+    auto entry = [](uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+        float re, im;
+        asm("{\n\t.reg .f16 a0, a1, b0, b1, c0, c1, d0, d1, na0, na1, nc0;\n\t"
+            "mov.b32 {a0, a1}, %2;\n\tmov.b32 {b0, b1}, %3;\n\tmov.b32 {c0, c1}, %4;\n\tmov.b32 {d0, d1}, %5;\n\t"
+            "neg.f16 na0, a0;\n\tneg.f16 na1, a1;\n\tneg.f16 nc0, c0;\n\t"
+            "fma.rn.f32.f16 %0, a0, b0, 0f00000000;\n\tfma.rn.f32.f16 %1, na0, b1, 0f00000000;\n\t"
+            "fma.rn.f32.f16 %0, na1, b1, %0;\n\tfma.rn.f32.f16 %1, na1, b0, %1;\n\t"
+            "fma.rn.f32.f16 %0, nc0, d0, %0;\n\tfma.rn.f32.f16 %1, c0, d1, %1;\n\t"
+            "fma.rn.f32.f16 %0, c1, d1, %0;\n\tfma.rn.f32.f16 %1, c1, d0, %1;\n\t}"
+            : "=f"(re), "=f"(im)
+            : "r"(a), "r"(b), "r"(c), "r"(d));
         return pack_half2(re, im);
     };
-    u[6] = entry(u[1], n1, u[5], i5, u[2], n2, u[4], i4);
-    u[7] = entry(u[2], n2, u[3], i3, u[0], n0, u[5], i5);
-    u[8] = entry(u[0], n0, u[4], i4, u[1], n1, u[3], i3);
+    u[6] = entry(u[1], u[5], u[2], u[4]);
+    u[7] = entry(u[2], u[3], u[0], u[5]);
+    u[8] = entry(u[0], u[4], u[1], u[3]);
 }
 
 // acc += coef * (the four-spinor reconstructed from w) for the projector
@@ -171,18 +207,11 @@ __device__ __forceinline__ void reconstruct16(float ar[12], float ai[12], const 
 __device__ __forceinline__ void clover_block16(const uint32_t b[18], const uint32_t x[6], float s, float o_r[6],
                                                float o_i[6])
 {
-    uint32_t ix[6], nix[6];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-        ix[a] = h2_times_i(x[a]);
-        nix[a] = h2_neg(ix[a]);
-    }
     float tr[6], ti[6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
-        const unsigned short d = (a & 1) ? h_hi(b[a >> 1]) : h_lo(b[a >> 1]);
-        tr[a] = mfma(d, h_lo(x[a]), 0.f);
-        ti[a] = mfma(d, h_hi(x[a]), 0.f);
+        if (a & 1) rmul16<true>(tr[a], ti[a], b[a >> 1], x[a]);
+        else rmul16<false>(tr[a], ti[a], b[a >> 1], x[a]);
     }
     int k = 3;
 #pragma unroll
@@ -190,8 +219,8 @@ __device__ __forceinline__ void clover_block16(const uint32_t b[18], const uint3
 #pragma unroll
         for (int c = 0; c < a; ++c) {
             const uint32_t L = b[k++];
-            cmac16(tr[a], ti[a], L, x[c], ix[c]);    // L_ac x_c
-            cjmac16(tr[c], ti[c], L, x[a], nix[a]);  // conj(L_ac) x_a
+            cmac16(tr[a], ti[a], L, x[c]);   // L_ac x_c
+            cjmac16(tr[c], ti[c], L, x[a]);  // conj(L_ac) x_a
         }
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
