@@ -567,6 +567,32 @@ def profile_kernel(which):
     __graft_entry__.build()
     from paper_2112_00501_gb300 import api, synth
 
+    if which in ("dslash_batch", "sap_batch"):
+        # the batched workload (12 + 8 + 8 right-hand sides on three lattices), its
+        # autotuned operator launch or one smoother sweep over the batch
+        bw = BATCH_WORKLOAD
+        ops, xs, nrhs = [], [], []
+        for bdims, nr in bw["lattices"]:
+            Ub = synth.gauge_field(bdims, bw["eps"], synth.gauge_seed(bw["config_index"]))
+            lat = api.Lattice(bdims, bw["block"], -1)
+            g = api.Gauge(lat, torch.from_numpy(Ub).cuda(), storage_prec=bw["prec"], compress=bw["compress"])
+            op = api.CloverOperator(g, bw["kappa"], bw["csw"])
+            bb = torch.from_numpy(synth.gaussian_spinor(bdims, synth.source_seed(bw["config_index"]), nrhs=nr)).cuda()
+            ops.append(op)
+            xs.append(lat.pack(bb, bw["prec"]))
+            nrhs.append(nr)
+        B = api.Batch(ops, nrhs)
+        B.tune(bw["prec"])
+        ys = B.empty_packed(bw["prec"])
+        zs = B.zeros_packed(bw["prec"])
+        for _ in range(2):
+            if which == "dslash_batch":
+                B.apply_D(xs, bw["prec"], out=ys)
+            else:
+                B.sap_smooth(xs, zs, bw["prec"], 1, bw["n_mr"], x_is_zero=False)
+        torch.cuda.synchronize()
+        print("profile run done")
+        return 0
     w = WORKLOAD
     dims = (24, 24, 24, 48)
     U = synth.gauge_field(dims, w["eps"], synth.gauge_seed(3))
@@ -606,7 +632,8 @@ def main():
     ap.add_argument("--no-qws", action="store_true")
     ap.add_argument("--no-mg", action="store_true")
     ap.add_argument("--no-c1", action="store_true")
-    ap.add_argument("--profile-kernel", choices=["sap", "sap32", "dslash", "dslash32", "dslash16x18", "dslash64"],
+    ap.add_argument("--profile-kernel", choices=["sap", "sap32", "dslash", "dslash32", "dslash16x18", "dslash64",
+                                                 "dslash_batch", "sap_batch"],
                     default=None,
                     help="run only a few launches of one kernel on 24^3x48 (for ncu captures)")
     args = ap.parse_args()
