@@ -296,34 +296,54 @@ __device__ __forceinline__ void clover16_site(const Clover16 &C, int i, const ui
     clover_planes16<true>(q, (size_t)1 << C.lvb, v, s, ar, ai);
 }
 
+// acc += mk (the hop from x + mu along MU) with the link words u of U_mu(x),
+// the neighbour's scale and the t-boundary sign in the coefficient
+template <int MU, bool DAG>
+__device__ __forceinline__ void hop16_fwd_u(const Geom &g, const int c[4], const Spinor16 &in, const uint32_t u[9],
+                                            float mk, float ar[12], float ai[12])
+{
+    constexpr int SF = DAG ? +1 : -1;
+    bool wr;
+    uint32_t s[12], h[6];
+    float wre[6], wim[6];
+    const int j = neighbour(g, c, MU, +1, &wr);
+    words16(in, j, s);
+    float coef = mk * in.scale_of(j);
+    if (MU == 3 && wr && g.tbc < 0) coef = -coef;
+    project16<MU, SF>(s, h);
+    su3_mul16<false>(u, h, wre, wim);
+    reconstruct16<MU, SF>(ar, ai, wre, wim, coef);
+}
+
+// acc += mk (the hop from x - mu along MU), U_mu(x - mu) from global memory
+template <int MU, bool DAG, class GA>
+__device__ __forceinline__ void hop16_back(const Geom &g, const int c[4], const Spinor16 &in, const GA &U, float mk,
+                                           float ar[12], float ai[12])
+{
+    constexpr int SB = DAG ? -1 : +1;
+    bool wr;
+    uint32_t s[12], h[6], u[9];
+    float wre[6], wim[6];
+    const int j = neighbour(g, c, MU, -1, &wr);
+    words16(in, j, s);
+    float coef = mk * in.scale_of(j);
+    if (MU == 3 && wr && g.tbc < 0) coef = -coef;
+    project16<MU, SB>(s, h);
+    links16(U, j, MU, u);
+    su3_mul16<true>(u, h, wre, wim);
+    reconstruct16<MU, SB>(ar, ai, wre, wim, coef);
+}
+
 // acc += -kappa (the two hops along MU), each with its neighbour's scale and
 // the t-boundary sign in the coefficient
 template <int MU, bool DAG, class GA>
 __device__ __forceinline__ void hop16_dir(const Geom &g, const int c[4], int i, const Spinor16 &in, const GA &U,
                                           float mk, float ar[12], float ai[12])
 {
-    constexpr int SF = DAG ? +1 : -1;
-    constexpr int SB = -SF;
-    bool wr;
-    uint32_t s[12], h[6], u[9];
-    float wre[6], wim[6];
-    int j = neighbour(g, c, MU, +1, &wr);
-    words16(in, j, s);
-    float coef = mk * in.scale_of(j);
-    if (MU == 3 && wr && g.tbc < 0) coef = -coef;
-    project16<MU, SF>(s, h);
+    uint32_t u[9];
     links16(U, i, MU, u);
-    su3_mul16<false>(u, h, wre, wim);
-    reconstruct16<MU, SF>(ar, ai, wre, wim, coef);
-
-    j = neighbour(g, c, MU, -1, &wr);
-    words16(in, j, s);
-    coef = mk * in.scale_of(j);
-    if (MU == 3 && wr && g.tbc < 0) coef = -coef;
-    project16<MU, SB>(s, h);
-    links16(U, j, MU, u);
-    su3_mul16<true>(u, h, wre, wim);
-    reconstruct16<MU, SB>(ar, ai, wre, wim, coef);
+    hop16_fwd_u<MU, DAG>(g, c, in, u, mk, ar, ai);
+    hop16_back<MU, DAG>(g, c, in, U, mk, ar, ai);
 }
 
 }  // namespace mgc
