@@ -227,9 +227,11 @@ int mgc_sap_smooth_A(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy
  * single-precision solver).  Methods:
  *   0  FGCR(restart) with FP64 Krylov vectors, FP64 D in every iteration;
  *   1  flexible BiCGStab (the paper's outer solver) with FP64 vectors;
- *   2  two-level: FP64 defect correction (residual b - D x, D and x in FP64)
- *      around an FP32 FGCR(restart) + SAP inner solve to inner_tol, whose
- *      inner products accumulate in FP64 across the lattice;
+ *   2  two-level: FP64 defect correction (residual b - D x, D, x and the
+ *      residual norm in FP64) around an FP32 FGCR(restart) + SAP inner solve
+ *      to inner_tol: FP32 Krylov vectors and orthogonalisation, inner
+ *      products summed in FP32 over a few entries per thread and in FP64
+ *      across the lattice, FP64 Gram-Schmidt coefficients;
  *   3  QWS (Sec. 2): FP64 Richardson on b - D x around an FP32 BiCGStab on
  *      A M_SAP (A = C^-1 D, source C^-1 r, M_SAP from mgc_sap_smooth_A with
  *      n_mr Jacobi iterations per domain) to inner_tol; x += ||C^-1 r|| M_SAP y.
@@ -260,8 +262,11 @@ void mgc_solve_params_default(mgc_solve_params *p);
 
 /*
  * Solve D x = b for nrhs canonical complex128 right-hand sides (one after the
- * other).  FP64 vectors, inner products, orthogonalisation and residual
- * updates; the SAP preconditioner in smoother_prec.  Synchronises stream.
+ * other) with the method of p (above): methods 0, 1 and the outer iteration
+ * of 3 keep their vectors, inner products, orthogonalisation and residual
+ * updates in FP64; method 2 keeps its residual, x and norms in FP64 and runs
+ * its inner solve in FP32 (above); the SAP preconditioner in smoother_prec.
+ * Synchronises stream.
  * Host pointers (on_device = 0): with x in page-locked memory, method 2
  * copies x back on a stream of its own while the FP64 residual that confirms
  * convergence is computed; x holds the solution once the call returns, as
