@@ -302,15 +302,18 @@ FORCE_WORKLOAD = dict(dims=(24, 24, 24, 48), block=(4, 4, 4, 4), eps=0.4, kappa=
                       prec=32, compress=18)
 
 
-def bench_batch(lib, stream):
+def bench_batch(lib, stream, prec=None, compress=None):
     """The batched workload: batched D and smoother against one launch per
     lattice, and the lock-step batched solve of all systems against solving
-    them one after another."""
+    them one after another; at the workload's storage unless prec/compress
+    are given."""
     import torch
 
     from paper_2112_00501_gb300 import api, synth
 
-    bw = BATCH_WORKLOAD
+    bw = dict(BATCH_WORKLOAD)
+    if prec is not None:
+        bw["prec"], bw["compress"] = prec, compress
     ops, bs, nrhs = [], [], []
     for dims, nr in bw["lattices"]:
         U = synth.gauge_field(dims, bw["eps"], synth.gauge_seed(bw["config_index"]))
@@ -321,8 +324,10 @@ def bench_batch(lib, stream):
                                                          nrhs=nr)).cuda())
         nrhs.append(nr)
     B = api.Batch(ops, nrhs)
+    storage = ("FP32 storage" if bw["prec"] == 32 else
+               f"FP16 storage + per-site scale, {bw['compress']}-real links")
     out = {"workload": " + ".join(f"{nr} RHS on {'x'.join(map(str, d))}" for d, nr in bw["lattices"]) +
-           f", eps={bw['eps']}, kappa={bw['kappa']}, c_sw={bw['csw']}, FP32 storage, FP32 smoother "
+           f", eps={bw['eps']}, kappa={bw['kappa']}, c_sw={bw['csw']}, {storage}, FP32 smoother arithmetic "
            f"({bw['n_cy']} sweeps x {bw['n_mr']} MR, 4^4 domains) inside FP64 defect correction, "
            f"tol {bw['tol']:g}"}
     prec = bw["prec"]
@@ -913,6 +918,9 @@ def main():
     # ---------------- batched workload and link force (reported beside the headline)
     mgres = None if args.no_mg else bench_mg(lib, stream, op, b, params, w)
     batch = None if args.no_batch else bench_batch(lib, stream)
+    if batch is not None:
+        # the same batch at the benchmark's FP16 storage (FP32 arithmetic)
+        batch["fp16_storage"] = bench_batch(lib, stream, prec=16, compress=12)
     force = None if args.no_force else bench_force(lib, stream)
     c1 = None if args.no_c1 else bench_c1(lib, stream)
     counters(lib, reset=True)

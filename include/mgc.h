@@ -144,7 +144,10 @@ int mgc_clover_destroy(mgc_clover_t op);
  * on their own asynchronous copies give up after a bounded time and set a bit
  * here instead of hanging.  *flags receives the word; clear != 0 zeroes it.
  * Returns MGC_ERR_TIMEOUT when any bit is set.  Synchronises stream.
- * mgc_solve and mgc_force check it themselves.
+ * mgc_solve and mgc_force check it themselves.  After MGC_ERR_TIMEOUT the
+ * results of the calls since the last check are invalid and the operator
+ * must be destroyed, not reused: a copy that never completed may still land
+ * in memory the next launch uses.
  */
 int mgc_device_status(mgc_clover_t op, int *flags, int clear, void *stream);
 /*

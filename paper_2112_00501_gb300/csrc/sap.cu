@@ -878,6 +878,8 @@ __device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, c
 
     if (l == 0) mbar_init(bar, 1);
     __syncthreads();
+    static_assert(HL::STAGE * VB % 16 == 0 && 144 * VB % 16 == 0 && 4 * VB % 16 == 0,
+                  "bulk copies move multiples of 16 bytes");
     if (l == 0) {
         const unsigned lbytes = HL::STAGE * VB, cb = 144 * VB, sb = 4 * VB;
         mbar_arrive_expect_tx(bar, lbytes + cb + sb);
@@ -1407,6 +1409,7 @@ __device__ __forceinline__ void sap_f32_body(const Geom &g, const Spinor32 &b, c
 
     if (l == 0) mbar_init(bar, 1);
     __syncthreads();
+    static_assert(FL::STAGE * VB % 16 == 0, "bulk copies move multiples of 16 bytes");
     if (l == 0) {
         const unsigned lbytes = FL::STAGE * VB;
         mbar_arrive_expect_tx(bar, lbytes);
@@ -1853,6 +1856,14 @@ static int sap_launch_impl(const mgc_clover_s *op, int prec, const void *b, void
                              n_cy, n_it, x_is_zero, s, prec, ga->compress);
     }
     if (!has_prec(ga, prec)) return fail(MGC_ERR_INVALID_ARG, "no copy of the operator at this precision");
+    // the FP32/FP16 kernels stage each domain's links and clover term with 1-D
+    // bulk copies, which must start on 16-byte boundaries: the fields are
+    // allocated that way and every domain's share is a multiple of 16 bytes
+    const uintptr_t al = prec == 32 ? ((uintptr_t)ga->U32 | (uintptr_t)op->C32 | (uintptr_t)op->Ci32)
+                                    : ((uintptr_t)ga->U16 | (uintptr_t)op->C16 | (uintptr_t)op->C16_sc |
+                                       (uintptr_t)op->Ci16 | (uintptr_t)op->Ci16_sc);
+    if ((al & 15) || (1 << g.lvb) % 4)
+        return fail(MGC_ERR_INVALID_ARG, "smoother fields not aligned for bulk copies");
     const int cp = ga->compress;
     if (prec == 32) {
         Spinor32 B{(float4 *)b, g.lvb}, X{(float4 *)x, g.lvb};
