@@ -826,9 +826,9 @@ def main():
         del op64, g64
     counters(lib, reset=True)
 
-    # ---------------- FP64 FGCR (FP64 vectors, inner products and orthogonalisation)
-    # around the FP16 smoother: the benchmark definition's precision pattern
-    # taken literally, beside the default two-level solve
+    # ---------------- FP64 FGCR (FP64 vectors, inner products and orthogonalisation
+    # in every iteration) around the FP16 smoother, beside the default two-level
+    # solve whose inner solve works in FP32
     fgcr16 = None
     if not args.no_fp64_path:
         pf = api.solve_params(method=0, precond=1, smoother_prec=w["prec"], n_cy=w["n_cy"], n_mr=w["n_mr"],
