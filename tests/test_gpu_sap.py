@@ -31,18 +31,37 @@ def test_sap_matches_oracle(name, prec, compress):
     assert rel(got, ref) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [64, 32])
-def test_sap_from_nonzero_guess(prec):
+@pytest.mark.parametrize("prec,compress", [(64, 18), (32, 18), (16, 12)])
+def test_sap_from_nonzero_guess(prec, compress):
     from paper_2112_00501_gb300 import synth
 
     name = "mid_8^4"
     dims, block, eps, kappa, csw, U, psi = fields(name)
-    op, lat = _op(name, prec, 18)
+    op, lat = _op(name, prec, compress)
     x0 = synth.gaussian_spinor(dims, 321)
     got = op.sap(torch.from_numpy(psi).cuda(), prec=prec, n_cy=2, n_mr=3,
                  x0=torch.from_numpy(x0).cuda()).cpu().numpy()
     ref = O.sap(dims, block, -1, kappa, U, O.clover(dims, kappa, csw, U), psi, x0=x0, ncy=2, nmr=3)
     assert rel(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec,compress", [(32, 18), (16, 12), (16, 18)])
+def test_sap_several_rhs_in_one_call(prec, compress):
+    """Three right-hand sides in one call (one thread block per domain and
+    right-hand side, the FP16 scales of each field after all their planes):
+    each against the oracle's smoother on its own source."""
+    from paper_2112_00501_gb300 import synth
+
+    name = "mid_8^4"
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    op, lat = _op(name, prec, compress)
+    bs = synth.gaussian_spinor(dims, 4321, nrhs=3)
+    bs[1] *= 1e-3  # a right-hand side of another magnitude
+    got = op.sap(torch.from_numpy(bs).cuda(), prec=prec, n_cy=2, n_mr=4).cpu().numpy()
+    Cl = O.clover(dims, kappa, csw, U)
+    for q in range(3):
+        ref = O.sap(dims, block, -1, kappa, U, Cl, bs[q], ncy=2, nmr=4)
+        assert rel(got[q], ref) < TOL[prec], q
 
 
 def test_sap_degenerate_counts():
