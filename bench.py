@@ -529,14 +529,17 @@ def bench_c1(lib, stream):
     return res
 
 
-def bench_force(lib, stream):
+def bench_force(lib, stream, prec=None, compress=None):
     """dS/dU for S = phi^+ (D^+ D)^-1 phi on 24^3 x 48 (two solves and the
-    force kernels)."""
+    force kernels); the solves' smoother at the workload's storage unless
+    prec/compress are given."""
     import torch
 
     from paper_2112_00501_gb300 import api, synth
 
-    fw = FORCE_WORKLOAD
+    fw = dict(FORCE_WORKLOAD)
+    if prec is not None:
+        fw["prec"], fw["compress"] = prec, compress
     dims = fw["dims"]
     U = synth.gauge_field(dims, fw["eps"], synth.gauge_seed(fw["config_index"]))
     phi = torch.from_numpy(synth.gaussian_spinor(dims, synth.source_seed(fw["config_index"]))).cuda()
@@ -557,8 +560,9 @@ def bench_force(lib, stream):
     torch.cuda.nvtx.range_pop()
     t = e0.elapsed_time(e1) / 1e3 / n
     V = synth.volume(dims)
+    storage = "FP32 storage" if fw["prec"] == 32 else f"FP16 storage, {fw['compress']}-real links"
     return {"workload": f"{'x'.join(map(str, dims))}, eps={fw['eps']}, kappa={fw['kappa']}, c_sw={fw['csw']}, "
-                        f"two-level solves (FP32 smoother) to 1e-10",
+                        f"two-level solves (smoother: {storage}, FP32 arithmetic) to 1e-10, FP64 force kernels",
             "ms": 1e3 * t, "links_per_s": 4 * V / t, "solve_iters": info.iters}
 
 
@@ -922,6 +926,8 @@ def main():
         # the same batch at the benchmark's FP16 storage (FP32 arithmetic)
         batch["fp16_storage"] = bench_batch(lib, stream, prec=16, compress=12)
     force = None if args.no_force else bench_force(lib, stream)
+    if force is not None:
+        force["fp16_storage"] = bench_force(lib, stream, prec=16, compress=12)
     c1 = None if args.no_c1 else bench_c1(lib, stream)
     counters(lib, reset=True)
 
