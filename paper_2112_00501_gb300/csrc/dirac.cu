@@ -216,9 +216,16 @@ __global__ void __launch_bounds__(DIRAC_THREADS, (LVB > 0 && sizeof(typename SPI
     }
     int c[4];
     site_coords(gg, i, c);
-    Cx<T> o[12];
-    dirac_site_k<DAG>(gg, c, i, src, Ug, Cg, kappa, o);
-    dst.store(i, o);
+    if constexpr (sizeof(T) == 8) {
+        const SPI one[1] = {src};
+        Cx<T> o[1][12];
+        dirac_site_pair<DAG, 1>(gg, c, i, one, 1, Ug, Cg, kappa, o);
+        dst.store(i, o[0]);
+    } else {
+        Cx<T> o[12];
+        dirac_site_k<DAG>(gg, c, i, src, Ug, Cg, kappa, o);
+        dst.store(i, o);
+    }
 }
 
 // ---- the FP16 operator: FP16 links, clover and spinors with their per-site

@@ -82,6 +82,14 @@ __global__ void __launch_bounds__(256, dirac_batch_min_blocks<RB, SP>()) k_dirac
     site_coords(gg, i, c);
     Cx<T> acc[RB][12];
     const T kappa = B.kappa[k];
+    if constexpr (sizeof(T) == 8) {
+        // the single-RHS FP64 operator's arithmetic, right-hand side by right-hand side
+        dirac_site_pair<DAG, RB>(gg, c, i, src, nr, Ug, Cg, kappa, acc);
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+            if (q < nr) shift_rhs(base_out, r0 + q, gg.V).store(i, acc[q]);
+        return;
+    }
     hop_site_multi<DAG, RB>(gg, c, i, src, nr, Ug, -kappa, acc);
 #pragma unroll
     for (int q = 0; q < RB; ++q)

@@ -212,6 +212,131 @@ __device__ __forceinline__ void hop_site_multi(const Geom &g, const int c[4], in
     hop_dir_multi<3, DAG>(g, c, i, in, nr, U, mk, acc);
 }
 
+// ---- the FP64 operator's form, where every FP64 instruction counts (GB300
+// issues FP64 at 1/64 of the FP32 rate): the two hops along MU are combined
+// before they reach the accumulator.  With w_f = U_mu(x) h_f and
+// w_b = U_mu(x-mu)^+ h_b, and the two projector signs opposite, the upper
+// spins receive c (w_f + g w_b) and the lower spins sig c P(w_f - g w_b),
+// where P is the isigma map of the projection (identity for mu = t), sig its
+// sign, c the forward hop's coefficient and g = +-1 the ratio of the backward
+// hop's coefficient to it (-1 only where exactly one of the two hops wraps an
+// antiperiodic t boundary).  s = w_f + g w_b comes out of the backward mat-vec
+// accumulating onto w_f, and w_f - g w_b = 2 w_f - s, so a pair of hops takes
+// 204 FP64 instructions instead of 216.
+
+// s = w + U^dagger h (two colour vectors)
+template <typename T>
+__device__ __forceinline__ void su3_dag_mul_acc(const Cx<T> u[9], const Cx<T> h[6], const Cx<T> w[6], Cx<T> s[6])
+{
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Cx<T> acc = cjfma(u[a], h[3 * q], w[3 * q + a]);
+            acc = cjfma(u[3 + a], h[3 * q + 1], acc);
+            acc = cjfma(u[6 + a], h[3 * q + 2], acc);
+            s[3 * q + a] = acc;
+        }
+}
+
+// acc += c (s on the upper spins) + sig c P(2 w - s) on the lower spins, for
+// the forward projector 1 + SF gamma_mu
+template <int MU, int SF, typename T>
+__device__ __forceinline__ void reconstruct_pair(Cx<T> acc[12], const Cx<T> w[6], const Cx<T> s[6], T c)
+{
+    const T lo = (MU == 3 ? (SF > 0 ? -c : c) : (SF > 0 ? c : -c));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        acc[k] = Cx<T>{fma(c, s[k].r, acc[k].r), fma(c, s[k].i, acc[k].i)};
+        acc[3 + k] = Cx<T>{fma(c, s[3 + k].r, acc[3 + k].r), fma(c, s[3 + k].i, acc[3 + k].i)};
+        const Cx<T> d0 = {fma(T(2), w[k].r, -s[k].r), fma(T(2), w[k].i, -s[k].i)};
+        const Cx<T> d1 = {fma(T(2), w[3 + k].r, -s[3 + k].r), fma(T(2), w[3 + k].i, -s[3 + k].i)};
+        Cx<T> o0, o1;
+        isigma<MU>(d0, d1, o0, o1);
+        acc[6 + k] = Cx<T>{fma(lo, o0.r, acc[6 + k].r), fma(lo, o0.i, acc[6 + k].i)};
+        acc[9 + k] = Cx<T>{fma(lo, o1.r, acc[9 + k].r), fma(lo, o1.i, acc[9 + k].i)};
+    }
+}
+
+// acc[q] += mk * (the two hops along MU) for the first nr of RB right-hand
+// sides, both links loaded once; RB = 1 is the single-RHS operator
+template <int MU, bool DAG, int RB, class SP, class GA, typename T>
+__device__ __forceinline__ void hop_pair_multi(const Geom &g, const int c[4], int i, const SP (&in)[RB], int nr,
+                                               const GA &U, T mk, Cx<T> (&acc)[RB][12])
+{
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    bool wf, wb;
+    const int jf = neighbour(g, c, MU, +1, &wf);
+    const int jb = neighbour(g, c, MU, -1, &wb);
+    const bool ff = MU == 3 && wf && g.tbc < 0, fb = MU == 3 && wb && g.tbc < 0;
+    const T cf = ff ? -mk : mk;
+    Cx<T> uf[9], ub[9];
+    U.load(i, MU, uf);
+    U.load(jb, MU, ub);
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+        if (q < nr) {
+            Cx<T> h[6], w[6], s[6];
+            load_project_s<MU, SF>(in[q], jf, h);
+            su3_mul(uf, h, w);
+            load_project_s<MU, SB>(in[q], jb, h);
+            if (ff != fb) negate6(h);
+            su3_dag_mul_acc(ub, h, w, s);
+            reconstruct_pair<MU, SF>(acc[q], w, s, cf);
+        }
+}
+
+// out += C in for the packed clover c[72] (the accumulating form of clover_mul)
+template <typename T>
+__device__ __forceinline__ void clover_mul_acc(const T c[72], const Cx<T> in[12], Cx<T> out[12])
+{
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+        const T *d = c + 36 * chi;
+        const Cx<T> *v = in + 6 * chi;
+        Cx<T> *o = out + 6 * chi;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) o[a] = Cx<T>{fma(d[a], v[a].r, o[a].r), fma(d[a], v[a].i, o[a].i)};
+        int k = 6;
+#pragma unroll
+        for (int a = 1; a < 6; ++a)
+#pragma unroll
+            for (int b = 0; b < a; ++b) {
+                const Cx<T> L = {d[k], d[k + 1]};
+                k += 2;
+                o[a] = cfma(L, v[b], o[a]);
+                o[b] = cjfma(L, v[a], o[b]);
+            }
+    }
+}
+
+// (D psi)(x) for RB right-hand sides at FP64 (unit scales): the paired hops
+// with -kappa as their coefficient, then C psi accumulated onto them
+template <bool DAG, int RB, class SP, class GA, class CL, typename T>
+__device__ __forceinline__ void dirac_site_pair(const Geom &g, const int c[4], int i, const SP (&in)[RB], int nr,
+                                                const GA &U, const CL &C, T kappa, Cx<T> (&out)[RB][12])
+{
+    static_assert(sizeof(T) == 8, "the paired form is the FP64 operator's");
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[q][k] = Cx<T>{0, 0};
+    hop_pair_multi<0, DAG>(g, c, i, in, nr, U, -kappa, out);
+    hop_pair_multi<1, DAG>(g, c, i, in, nr, U, -kappa, out);
+    hop_pair_multi<2, DAG>(g, c, i, in, nr, U, -kappa, out);
+    hop_pair_multi<3, DAG>(g, c, i, in, nr, U, -kappa, out);
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+        if (q < nr) {
+            T cl[72];
+            Cx<T> psi[12];
+            C.load(i, cl);  // per right-hand side: 144 registers do not stay live across them
+            in[q].load(i, psi);
+            clover_mul_acc(cl, psi, out[q]);
+        }
+}
+
 // out = C(i) psi
 template <class CL, typename T>
 __device__ __forceinline__ void clover_site(const CL &C, int i, const Cx<T> psi[12], Cx<T> out[12])

@@ -67,15 +67,18 @@ __device__ __forceinline__ void rmul16(float &re, float &im, uint32_t dw, uint32
             : "r"(dw), "r"(x));
 }
 
+// a + b and a - b on packed halves, rounded to nearest
 __device__ __forceinline__ uint32_t h2_add(uint32_t a, uint32_t b)
 {
-    __half2 r = __hadd2(*reinterpret_cast<__half2 *>(&a), *reinterpret_cast<__half2 *>(&b));
-    return *reinterpret_cast<uint32_t *>(&r);
+    uint32_t d;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
 }
 __device__ __forceinline__ uint32_t h2_sub(uint32_t a, uint32_t b)
 {
-    __half2 r = __hsub2(*reinterpret_cast<__half2 *>(&a), *reinterpret_cast<__half2 *>(&b));
-    return *reinterpret_cast<uint32_t *>(&r);
+    uint32_t d;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
 }
 
 // z + i w and z - i w on packed halves: w's halves swapped and scaled by

@@ -1048,8 +1048,43 @@ __device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, c
 // FP16, as it sees every FP16-stored spinor.  Shared memory as in k_sap_h16,
 // the r area holding the FP16 copy of r and its scales.
 
-template <int MU, int SGN, int VB>
-__device__ __forceinline__ void m16_hop(const uint4 *r16, const float *rsc, int n, const uint32_t *sL, int lk, float mk,
+// The staged links of one domain in shared memory, as half2 words, entry k of
+// link (lk, mu) at word k.  Links rebuilt from 12 reals in the kernel are
+// stored packed ([4][2][VB] uint4 for words 0-7, then [4][VB] words 8), so a
+// link takes three shared-memory loads; 18-real links keep their global
+// layout ([4][9][VB] words), into which they are copied whole.
+template <bool PACKED, int VB> struct SmemLinks16 {
+    const uint32_t *w;
+    template <int MU> __device__ __forceinline__ void load(int lk, uint32_t u[9]) const
+    {
+        if (PACKED) {
+            const uint4 *w4 = reinterpret_cast<const uint4 *>(w);
+            const uint4 a = w4[(MU * 2) * VB + lk], b = w4[(MU * 2 + 1) * VB + lk];
+            u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+            u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+            u[8] = w[32 * VB + MU * VB + lk];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) u[k] = w[(MU * 9 + k) * VB + lk];
+        }
+    }
+    __device__ __forceinline__ void store(int mu, int l, const uint32_t u[9]) const
+    {
+        uint32_t *d = const_cast<uint32_t *>(w);
+        if (PACKED) {
+            uint4 *d4 = reinterpret_cast<uint4 *>(d);
+            d4[(mu * 2) * VB + l] = make_uint4(u[0], u[1], u[2], u[3]);
+            d4[(mu * 2 + 1) * VB + l] = make_uint4(u[4], u[5], u[6], u[7]);
+            d[32 * VB + mu * VB + l] = u[8];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) d[(mu * 9 + k) * VB + l] = u[k];
+        }
+    }
+};
+
+template <int MU, int SGN, int VB, class SL>
+__device__ __forceinline__ void m16_hop(const uint4 *r16, const float *rsc, int n, const SL &sL, int lk, float mk,
                                         float ar[12], float ai[12])
 {
     uint32_t s[12], h[6], u[9];
@@ -1063,8 +1098,7 @@ __device__ __forceinline__ void m16_hop(const uint4 *r16, const float *rsc, int 
     }
     const float coef = mk * rsc[n];
     project16<MU, SGN>(s, h);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) u[k] = sL[(MU * 9 + k) * VB + lk];
+    sL.template load<MU>(lk, u);
     float wr[6], wi[6];
     su3_mul16<(SGN > 0)>(u, h, wr, wi);
     reconstruct16<MU, SGN>(ar, ai, wr, wi, coef);
@@ -1097,8 +1131,9 @@ __device__ __forceinline__ void sap_m16_body(const Geom &g, const Spinor16 &b, c
     constexpr int LB = LVB / 4;
     using HL = H16Links<GA>;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint32_t *sL = reinterpret_cast<uint32_t *>(smem);     // [4][9][VB] half2
-    uint4 *sC = reinterpret_cast<uint4 *>(sL + 36 * VB);   // [9][VB]
+    uint32_t *sLw = reinterpret_cast<uint32_t *>(smem);    // 36 VB half2 words of links
+    const SmemLinks16<HL::EXPAND, VB> sL{sLw};
+    uint4 *sC = reinterpret_cast<uint4 *>(sLw + 36 * VB);  // [9][VB]
     float *sS = reinterpret_cast<float *>(sC + 9 * VB);    // [VB]
     uint4 *area = reinterpret_cast<uint4 *>(sS + VB);      // 96 VB bytes: 12-real link stage, then r
     uint4 *r16 = area;                                     // [3][VB] FP16 copy of r
@@ -1137,7 +1172,7 @@ __device__ __forceinline__ void sap_m16_body(const Geom &g, const Spinor16 &b, c
     if (l == 0) {
         const unsigned lbytes = HL::STAGE * VB, cb = 144 * VB, sb = 4 * VB;
         mbar_arrive_expect_tx(bar, lbytes + cb + sb);
-        bulk_g2s(HL::EXPAND ? (void *)area : (void *)sL, HL::src(U, blk, LVB), lbytes, bar);
+        bulk_g2s(HL::EXPAND ? (void *)area : (void *)sLw, HL::src(U, blk, LVB), lbytes, bar);
         bulk_g2s(sC, C.p + ((size_t)blk * 9 << LVB), cb, bar);
         bulk_g2s(sS, C.sc + ((size_t)blk << LVB), sb, bar);
     }
@@ -1177,8 +1212,7 @@ __device__ __forceinline__ void sap_m16_body(const Geom &g, const Spinor16 &b, c
                 u[2 * k + 1] = v.y;
             }
             row2_16(u);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) sL[(mu * 9 + k) * VB + l] = u[k];
+            sL.store(mu, l, u);
         }
         __syncthreads();  // links complete, r area free
     }
