@@ -70,6 +70,39 @@ __device__ __forceinline__ void block_sum3(T &a, T &b, T &c, T *red)
     }
 }
 
+// block_sum3 for blocks of NT threads, NT a multiple of 128, with float
+// partials in a 16-byte aligned red: the warps' partials read back as float4
+template <int NT>
+__device__ __forceinline__ void block_sum3_v4(float &a, float &b, float &c, float *red)
+{
+    static_assert(NT % 128 == 0, "four warps per float4 of partials");
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[warp] = a;
+        red[32 + warp] = b;
+        red[64 + warp] = c;
+    }
+    __syncthreads();
+    const float4 *r4 = reinterpret_cast<const float4 *>(red);
+    float4 sa = r4[0], sb = r4[8], sc = r4[16];
+#pragma unroll
+    for (int w = 1; w < NT / 128; ++w) {
+        const float4 x = r4[w], y = r4[8 + w], z = r4[16 + w];
+        sa = make_float4(sa.x + x.x, sa.y + x.y, sa.z + x.z, sa.w + x.w);
+        sb = make_float4(sb.x + y.x, sb.y + y.y, sb.z + y.z, sb.w + y.w);
+        sc = make_float4(sc.x + z.x, sc.y + z.y, sc.z + z.z, sc.w + z.w);
+    }
+    a = (sa.x + sa.y) + (sa.z + sa.w);
+    b = (sb.x + sb.y) + (sb.z + sb.w);
+    c = (sc.x + sc.y) + (sc.z + sc.w);
+}
+
 // p = D_B r at local site l, r from shared memory rs[12][Vb]
 template <int MU, class GA, typename T>
 __device__ __forceinline__ void block_hop_dir(const GA &U, int blkbase, int i, int nf, int nb, const Cx<T> *rs,
@@ -1109,9 +1142,15 @@ __device__ __forceinline__ void m16_hop(const uint4 *r16, const float *rsc, int 
 template <int VB>
 __device__ __forceinline__ void m16_store_r(uint4 *r16, float *rsc, int l, const float rr[12], const float ri[12])
 {
-    float m = 0.f;
+    // the largest |component| by a tree of maxima
+    float t[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(rr[k]), fabsf(ri[k])));
+    for (int k = 0; k < 12; ++k) t[k] = fmaxf(fabsf(rr[k]), fabsf(ri[k]));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) t[k] = fmaxf(t[k], t[k + 6]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = fmaxf(t[k], t[k + 3]);
+    const float m = fmaxf(fmaxf(t[0], t[1]), t[2]);
     const float inv = m > 0.f ? 1.0f / m : 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -1274,15 +1313,22 @@ __device__ __forceinline__ void sap_m16_body(const Geom &g, const Spinor16 &b, c
         if (nb[2] >= 0) m16_hop<2, +1, VB>(r16, rsc, nb[2], sL, nb[2], mk, ar, ai);
         if (nf[3] >= 0) m16_hop<3, -1, VB>(r16, rsc, nf[3], sL, l, mk, ar, ai);
         if (nb[3] >= 0) m16_hop<3, +1, VB>(r16, rsc, nb[3], sL, nb[3], mk, ar, ai);
-        float pr = 0.f, pi = 0.f, pp = 0.f;
+        // <p, r> and <p, p> in four partial sums each (shorter dependent chains)
+        float sr[4] = {0.f, 0.f, 0.f, 0.f}, si[4] = {0.f, 0.f, 0.f, 0.f}, sp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            pr = fmaf(ar[k], rvr[k], fmaf(ai[k], rvi[k], pr));
-            pi = fmaf(ar[k], rvi[k], fmaf(-ai[k], rvr[k], pi));
-            pp = fmaf(ar[k], ar[k], fmaf(ai[k], ai[k], pp));
+            const int q = k & 3;
+            sr[q] = fmaf(ar[k], rvr[k], fmaf(ai[k], rvi[k], sr[q]));
+            si[q] = fmaf(ar[k], rvi[k], fmaf(-ai[k], rvr[k], si[q]));
+            sp[q] = fmaf(ar[k], ar[k], fmaf(ai[k], ai[k], sp[q]));
         }
-        block_sum3(pr, pi, pp, red);
-        const float alr = pp > 0.f ? pr / pp : 0.f, ali = pp > 0.f ? pi / pp : 0.f;
+        float pr = (sr[0] + sr[1]) + (sr[2] + sr[3]);
+        float pi = (si[0] + si[1]) + (si[2] + si[3]);
+        float pp = (sp[0] + sp[1]) + (sp[2] + sp[3]);
+        if constexpr (VB >= 128) block_sum3_v4<VB>(pr, pi, pp, red);
+        else block_sum3(pr, pi, pp, red);
+        const float ipp = pp > 0.f ? 1.0f / pp : 0.f;
+        const float alr = pr * ipp, ali = pi * ipp;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             er[k] = fmaf(alr, rvr[k], fmaf(-ali, rvi[k], er[k]));
