@@ -198,3 +198,41 @@ def test_batch_rejects_mixed_formats_and_methods():
         B.solve([torch.from_numpy(psi).cuda()], method=1)
     with pytest.raises(MgcError):
         B.apply_D([a[0].lattice.zeros_packed(16, nr)], 16)  # no FP16 copy
+
+
+# the benchmark's batch: 12 RHS on 24^3 x 48, 8 on 16^4, 8 on 8^4 (FP32 storage,
+# 18-real links, 4^4 domains), in the launch shape bench.py times
+C3 = [((24, 24, 24, 48), 12), ((16, 16, 16, 16), 8), ((8, 8, 8, 8), 8)]
+
+
+def test_full_size_batched_D_sampled_sites():
+    """The full-size batch in one launch (two RHS per thread, 128-thread
+    blocks, the RHS groups of a site block adjacent): bit for bit the
+    per-lattice operator, and on sampled sites of every RHS the oracle's D
+    computed site by site."""
+    from paper_2112_00501_gb300 import api
+
+    ops, xs, fields = [], [], []
+    for k, (dims, nr) in enumerate(C3):
+        U = synth.gauge_field(dims, EPS, synth.gauge_seed(40 + k))
+        psi = synth.gaussian_spinor(dims, synth.source_seed(40 + k), nrhs=nr)
+        lat = api.Lattice(dims, BLOCK, -1)
+        g = api.Gauge(lat, torch.from_numpy(U).cuda(), storage_prec=32, compress=18)
+        ops.append(api.CloverOperator(g, KAPPA, CSW))
+        xs.append(lat.pack(torch.from_numpy(psi).cuda(), 32))
+        fields.append((dims, nr, U, psi))
+    B = api.Batch(ops, [nr for _, nr in C3])
+    B.set_shape(32, 2, 128, 1, 1)
+    out = B.apply_D(xs, 32)
+    torch.cuda.synchronize()
+    for k, (op, (dims, nr, U, psi)) in enumerate(zip(ops, fields)):
+        assert torch.equal(out[k], op.apply_D(xs[k], 32, nr)), k
+        V = synth.volume(dims)
+        sites = synth.rng(90 + k).choice(V, 96, replace=False)
+        sites = np.concatenate([sites, [0, V - 1]])
+        got = op.lattice.unpack(out[k], 32, nr).reshape(nr, V, 4, 3)[:, torch.from_numpy(sites).cuda()]
+        got = got.cpu().numpy()
+        for q in range(nr):
+            ref = O.dirac_at(dims, -1, KAPPA, CSW, U, psi[q], sites)
+            assert rel(got[q], ref) < TOL[32], (k, q)
+        del psi
