@@ -1215,6 +1215,12 @@ __device__ __forceinline__ void sap_m16_body(const Geom &g, const Spinor16 &b, c
         bulk_g2s(sC, C.p + ((size_t)blk * 9 << LVB), cb, bar);
         bulk_g2s(sS, C.sc + ((size_t)blk << LVB), sb, bar);
     }
+    // launched as a programmatic dependent of the previous colour launch:
+    // let the next launch take the SMs this one frees, and read x (written
+    // by the previous launch) only once that launch has completed; the links
+    // and clover copies above do not depend on it
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     int lc[4], cg[4];
     local_coords(gg, l, lc);
@@ -1370,10 +1376,28 @@ static int sap_run_h16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clo
     auto kern = JAC ? k_sap_h16<JAC, LVB, GA> : k_sap_m16<LVB, GA>;
     MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(g.nblocks / 2, nrhs);
+    // the MR kernel's colour launches after the first are programmatic
+    // dependents of the one before (griddepcontrol in the kernel): their
+    // blocks start, and stage their links and clover, while the previous
+    // launch's last blocks run
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(1 << LVB);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = pdl;
+    cfg.numAttrs = 1;
     for (int cy = 0; cy < n_cy; ++cy)
         for (int colour = 0; colour < 2; ++colour) {
             const int xz = (cy == 0 && colour == 0) ? x_is_zero : 0;
-            kern<<<grid, 1 << LVB, smem, s>>>(g, b, x, U, C, (float)op->kappa, colour, n_mr, xz, op->d_status);
+            if (!JAC && (cy > 0 || colour > 0))
+                MGC_CUDA(cudaLaunchKernelEx(&cfg, kern, g, b, x, U, C, (float)op->kappa, colour, n_mr, xz,
+                                            op->d_status));
+            else
+                kern<<<grid, 1 << LVB, smem, s>>>(g, b, x, U, C, (float)op->kappa, colour, n_mr, xz, op->d_status);
             count(1, sap_launch_bytes(g, 16, compress, nrhs, xz != 0));
         }
     MGC_CUDA(cudaGetLastError());
