@@ -104,42 +104,78 @@ __global__ void k_force_N(Geom g, Spinor64 X, Spinor64 Y, double2 *N)
 }
 
 
-// where a factor of a plaquette term sits relative to site c: a link
-// (shifts along d0, d1; its direction; daggered or not) or an insertion N
-struct LinkRef {
-    int d0, s0, d1, s1, dir;
-    bool dag;
-};
-struct NRef {
-    int d0, s0, d1, s1;
-};
-
-// R = N0 M1 M2 M3 + M1 N1 M2 M3 + M1 M2 N2 M3 + M1 M2 M3 N3 with shared
-// prefixes, each factor loaded just before its product, so that four 3x3
-// matrices are live at a time (preloading all seven factors made the kernel
-// spill)
-__device__ void corner_sum(const Gauge64 &U, const double2 *N, const Geom &g, const int c[4], int p,
-                                const LinkRef m[3], const NRef n[4], cd *R)
+// The clover-leaf terms of all four links of one plaquette at once.  For the
+// plaquette at x in the plane (mu, nu), mu < nu, with links in loop order
+// A = U_mu(x), B = U_nu(x+mu), C = U_mu(x+nu)^+, D = U_nu(x)^+ and the
+// insertions N0..N3 = N_{mu nu} at its corners x, x+mu, x+mu+nu, x+nu, the
+// term of each link is the product of the other three in loop order after it
+// with N inserted at each corner in turn (the R of the header).  With
+// E_A = N0 A + A N1, E_B = N1 B + B N2, E_C = N2 C + C N3, E_D = N3 D + D N0:
+//   R_A = E_B CD + BC E_D,  R_B = E_C DA + CD E_A,
+//   R_C = E_D AB + DA E_B,  R_D = E_A BC + AB E_C,
+// 20 matrix products for the four links against 32 one link at a time.
+// R_X goes to Rb[((p * 4 + X) * 9 + e) * V + i] (X = A, B, C, D as 0..3).
+__global__ void __launch_bounds__(128) k_force_plaq(Geom g, Gauge64 U, const double2 *N, double2 *Rb)
 {
-    cd A[9], B[9], T[9], P[9];
-    f_link(U, g, c, m[0].d0, m[0].s0, m[0].d1, m[0].s1, m[0].dir, m[0].dag, A);  // M1
-    f_N(N, g, c, n[0].d0, n[0].s0, n[0].d1, n[0].s1, p, B);
-    f_m3mul(B, A, T);  // N0 M1
-    f_N(N, g, c, n[1].d0, n[1].s0, n[1].d1, n[1].s1, p, B);
-    f_m3mul(A, B, P);
-    for (int k = 0; k < 9; ++k) T[k] = T[k] + P[k];  // N0 M1 + M1 N1
-    f_link(U, g, c, m[1].d0, m[1].s0, m[1].d1, m[1].s1, m[1].dir, m[1].dag, B);  // M2
-    f_m3mul(A, B, P);  // M1 M2
-    f_m3mul(T, B, A);  // (..) M2
-    f_N(N, g, c, n[2].d0, n[2].s0, n[2].d1, n[2].s1, p, B);
-    f_m3mul(P, B, T);
-    for (int k = 0; k < 9; ++k) T[k] = A[k] + T[k];  // (..) M2 + M1 M2 N2
-    f_link(U, g, c, m[2].d0, m[2].s0, m[2].d1, m[2].s1, m[2].dir, m[2].dag, B);  // M3
-    f_m3mul(P, B, A);  // M1 M2 M3
-    f_m3mul(T, B, P);  // (..) M3
-    f_N(N, g, c, n[3].d0, n[3].s0, n[3].d1, n[3].s1, p, B);
-    f_m3mul(A, B, T);  // M1 M2 M3 N3
-    for (int k = 0; k < 9; ++k) R[k] = P[k] + T[k];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int p = blockIdx.y;
+    const int mu = p < 3 ? 0 : (p < 5 ? 1 : 2);
+    const int nu = p < 3 ? p + 1 : (p < 5 ? p - 1 : 3);
+    int c[4];
+    site_coords(g, i, c);
+    const size_t V = (size_t)g.V;
+    auto put = [&](int X, const cd *R) {
+        double2 *o = Rb + (size_t)(p * 4 + X) * 9 * V + i;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) o[e * V] = make_double2(R[e].r, R[e].i);
+    };
+    // the four products of neighbouring links
+    cd AB[9], BC[9], CD[9], DA[9];
+    {
+        cd X[9], Y[9];
+        f_link(U, g, c, mu, 0, nu, 0, mu, false, X);  // A
+        f_link(U, g, c, mu, 1, nu, 0, nu, false, Y);  // B
+        f_m3mul(X, Y, AB);
+        f_link(U, g, c, mu, 0, nu, 1, mu, true, X);   // C
+        f_m3mul(Y, X, BC);
+        f_link(U, g, c, mu, 0, nu, 0, nu, true, Y);   // D
+        f_m3mul(X, Y, CD);
+        f_link(U, g, c, mu, 0, nu, 0, mu, false, X);  // A
+        f_m3mul(Y, X, DA);
+    }
+    // E = N_start L + L N_end for link L between the corners (d0, s0) .. (d1, s1)
+    auto edge = [&](int l0, int l1, int ldir, bool dag, int a0, int a1, int b0, int b1, cd *E) {
+        cd L[9], Nm[9], T[9];
+        f_link(U, g, c, mu, l0, nu, l1, ldir, dag, L);
+        f_N(N, g, c, mu, a0, nu, a1, p, Nm);
+        f_m3mul(Nm, L, E);
+        f_N(N, g, c, mu, b0, nu, b1, p, Nm);
+        f_m3mul(L, Nm, T);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) E[k] = E[k] + T[k];
+    };
+    // R = P Q + S T
+    auto two = [&](const cd *P, const cd *Q, const cd *S, const cd *T, cd *R) {
+        cd W[9];
+        f_m3mul(P, Q, R);
+        f_m3mul(S, T, W);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = R[k] + W[k];
+    };
+    cd E1[9], E2[9], R[9];
+    edge(1, 0, nu, false, 1, 0, 1, 1, E1);  // E_B: B = U_nu(x+mu), corners x+mu .. x+mu+nu
+    edge(0, 0, nu, true, 0, 1, 0, 0, E2);   // E_D: D = U_nu(x)^+, corners x+nu .. x
+    two(E1, CD, BC, E2, R);
+    put(0, R);                              // R_A
+    two(E2, AB, DA, E1, R);
+    put(2, R);                              // R_C
+    edge(0, 0, mu, false, 0, 0, 1, 0, E1);  // E_A: A = U_mu(x), corners x .. x+mu
+    edge(0, 1, mu, true, 1, 1, 0, 1, E2);   // E_C: C = U_mu(x+nu)^+, corners x+mu+nu .. x+nu
+    two(E2, DA, CD, E1, R);
+    put(1, R);                              // R_B
+    two(E1, BC, AB, E2, R);
+    put(3, R);                              // R_D
 }
 
 __device__ __forceinline__ int plane_of(int a, int b)
@@ -178,7 +214,12 @@ __device__ void hop_force(const Geom &g, const int c[4], int i, const Spinor64 &
         }
 }
 
-__global__ void k_force(Geom g, Gauge64 U, Spinor64 X, Spinor64 Y, const double2 *N, double kappa, double csw,
+// g(x, mu): the hopping term, then the clover-leaf terms of the six
+// plaquettes that contain the link, read from k_force_plaq's output: in the
+// plane (mu, s), s > mu, the link is A of the plaquette at x and C of the one
+// at x - s; in the plane (s, mu), s < mu, it is B of the plaquette at x - s
+// and D of the one at x.  Undaggered links take conj(c') R^+, daggered c' R.
+__global__ void k_force(Geom g, Gauge64 U, Spinor64 X, Spinor64 Y, const double2 *Rb, double kappa, double csw,
                         double2 *out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -195,36 +236,30 @@ __global__ void k_force(Geom g, Gauge64 U, Spinor64 X, Spinor64 Y, const double2
 
     const cd cp = {0.0, -kappa * csw / 4.0};  // c'
     const cd cpc = conj(cp);
+    const size_t V = (size_t)g.V;
+    auto get = [&](int p, int Xr, int site, cd *R) {
+        const double2 *q = Rb + (size_t)(p * 4 + Xr) * 9 * V + site;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            const double2 v = q[e * V];
+            R[e] = cd{v.x, v.y};
+        }
+    };
     for (int sgm = 0; sgm < 4; ++sgm) {
         if (sgm == mu) continue;
         const int p = plane_of(mu, sgm);
+        int n[4] = {c[0], c[1], c[2], c[3]};
+        n[sgm] = (n[sgm] - 1 + g.L[sgm]) % g.L[sgm];
+        const int back = site_index(g, n);  // x - s
         cd R[9];
-        // undaggered plaquette
-        if (mu < sgm) {
-            // U_mu(y) U_s(y+mu) U_mu(y+s)^+ U_s(y)^+
-            const LinkRef m[3] = {{mu, 1, sgm, 0, sgm, false}, {mu, 0, sgm, 1, mu, true}, {mu, 0, sgm, 0, sgm, true}};
-            const NRef n[4] = {{mu, 1, sgm, 0}, {mu, 1, sgm, 1}, {mu, 0, sgm, 1}, {mu, 0, sgm, 0}};
-            corner_sum(U, N, g, c, p, m, n, R);
-        } else {
-            // U_s(y-s) U_mu(y) U_s(y-s+mu)^+ U_mu(y-s)^+
-            const LinkRef m[3] = {{sgm, -1, mu, 1, sgm, true}, {sgm, -1, mu, 0, mu, true}, {sgm, -1, mu, 0, sgm, false}};
-            const NRef n[4] = {{sgm, 0, mu, 1}, {sgm, -1, mu, 1}, {sgm, -1, mu, 0}, {sgm, 0, mu, 0}};
-            corner_sum(U, N, g, c, p, m, n, R);
-        }
+        // undaggered: A of the plaquette at x (mu < s) or B of the one at x - s (s < mu)
+        if (mu < sgm) get(p, 0, i, R);
+        else get(p, 1, back, R);
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) G[a * 3 + b] = G[a * 3 + b] + cpc * conj(R[b * 3 + a]);
-        // daggered plaquette
-        if (mu < sgm) {
-            // U_mu(y-s) U_s(y-s+mu) U_mu(y)^+ U_s(y-s)^+ ; after the link: y -> y-s -> y-s+mu -> y+mu
-            const LinkRef m[3] = {{mu, 0, sgm, -1, sgm, true}, {mu, 0, sgm, -1, mu, false}, {mu, 1, sgm, -1, sgm, false}};
-            const NRef n[4] = {{mu, 0, sgm, 0}, {mu, 0, sgm, -1}, {mu, 1, sgm, -1}, {mu, 1, sgm, 0}};
-            corner_sum(U, N, g, c, p, m, n, R);
-        } else {
-            // U_s(y) U_mu(y+s) U_s(y+mu)^+ U_mu(y)^+ ; after the link: y -> y+s -> y+s+mu -> y+mu
-            const LinkRef m[3] = {{sgm, 0, mu, 0, sgm, false}, {sgm, 1, mu, 0, mu, false}, {sgm, 0, mu, 1, sgm, true}};
-            const NRef n[4] = {{sgm, 0, mu, 0}, {sgm, 1, mu, 0}, {sgm, 1, mu, 1}, {sgm, 0, mu, 1}};
-            corner_sum(U, N, g, c, p, m, n, R);
-        }
+        // daggered: C of the plaquette at x - s (mu < s) or D of the one at x (s < mu)
+        if (mu < sgm) get(p, 2, back, R);
+        else get(p, 3, i, R);
         for (int k = 0; k < 9; ++k) G[k] = G[k] + cp * R[k];
     }
     double2 *o = out + (canon_index(g, c) * 4 + mu) * 9;
@@ -305,6 +340,7 @@ int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_par
     const size_t vb = spinor_bytes(g, 64, 1);
     const size_t gb = (size_t)g.V * 4 * 9 * sizeof(double2);
     double2 *phi64 = nullptr, *X = nullptr, *Y = nullptr, *T = nullptr, *N = nullptr, *stage = nullptr, *gout = nullptr;
+    double2 *Rb = nullptr;  // the plaquettes' clover-leaf terms, 24 matrices per site
     double *part = nullptr;
     int st = MGC_OK;
     mgc_solve_params q = *p;
@@ -313,7 +349,7 @@ int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_par
     const int nb = 512;
     auto cleanup = [&]() {
         cudaFree(phi64); cudaFree(X); cudaFree(Y); cudaFree(T); cudaFree(N); cudaFree(stage); cudaFree(gout);
-        cudaFree(part);
+        cudaFree(part); cudaFree(Rb);
     };
 #define FTRY(call)                         \
     do {                                   \
@@ -330,6 +366,7 @@ int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_par
     FCUDA(cudaMalloc(&Y, vb));
     FCUDA(cudaMalloc(&T, vb));
     FCUDA(cudaMalloc(&N, (size_t)g.V * 54 * sizeof(double2)));
+    FCUDA(cudaMalloc(&Rb, (size_t)g.V * 24 * 9 * sizeof(double2)));
     FCUDA(cudaMalloc(&part, 4 * nb * sizeof(double)));
     if (!p->on_device) {
         FCUDA(cudaMalloc(&stage, vb));
@@ -378,12 +415,15 @@ int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_par
     k_force_N<<<grid_for(g.V, 128), 128, 0, s>>>(g, Spinor64{X, g.lvb}, Spinor64{Y, g.lvb}, N);
     FCUDA(cudaGetLastError());
     count(1, (double)g.V * (2 * 192.0 + 54 * 16.0));
+    k_force_plaq<<<dim3(grid_for(g.V, 128), 6), 128, 0, s>>>(g, Gauge64{op->gauge->U64, g.lvb}, N, Rb);
+    FCUDA(cudaGetLastError());
+    count(1, (double)g.V * (576.0 + 54 * 16.0 + 24 * 144.0));
     double2 *dst = p->on_device ? (double2 *)dSdU : gout;
     dim3 grid(grid_for(g.V, 128), 4);
-    k_force<<<grid, 128, 0, s>>>(g, Gauge64{op->gauge->U64, g.lvb}, Spinor64{X, g.lvb}, Spinor64{Y, g.lvb}, N,
+    k_force<<<grid, 128, 0, s>>>(g, Gauge64{op->gauge->U64, g.lvb}, Spinor64{X, g.lvb}, Spinor64{Y, g.lvb}, Rb,
                                  op->kappa, op->csw, dst);
     FCUDA(cudaGetLastError());
-    count(1, (double)g.V * (2 * 192.0 + 54 * 16.0 + 576.0 + 576.0));
+    count(1, (double)g.V * (2 * 192.0 + 24 * 144.0 + 576.0));
     if (!p->on_device) FCUDA(cudaMemcpyAsync(dSdU, gout, gb, cudaMemcpyDeviceToHost, s));
     FCUDA(cudaStreamSynchronize(s));
     cleanup();
