@@ -71,31 +71,51 @@ __device__ __forceinline__ void f_N(const double2 *N, const Geom &g, const int c
     }
 }
 
-// N_{mu nu}(x) = M + M^+ for the six planes
-__global__ void k_force_N(Geom g, Spinor64 X, Spinor64 Y, double2 *N)
+// N_{mu nu}(x) = M + M^+ for the six planes.  Each chiral block of sigma is
+// a signed Pauli matrix: two of its four entries vanish and the others are
+// +-1 or +-i, so with the loops unrolled over the constant table a nonzero
+// entry costs the four multiply-adds of X_t conj(Y_s) into M and a zero one
+// nothing.
+__global__ void __launch_bounds__(128) k_force_N(Geom g, Spinor64 X, Spinor64 Y, double2 *N)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.V) return;
     cd x[12], y[12];
     X.load(i, x);
     Y.load(i, y);
+#pragma unroll
     for (int p = 0; p < 6; ++p) {
         cd M[9];
-        for (int b = 0; b < 3; ++b)
-            for (int a = 0; a < 3; ++a) {
-                cd acc = {0, 0};
-                for (int chi = 0; chi < 2; ++chi)
-                    for (int s = 0; s < 2; ++s)
-                        for (int t = 0; t < 2; ++t) {
-                            const cd sg = {c_sigma[chi][p][s][t][0], c_sigma[chi][p][s][t][1]};
-                            const cd xt = x[(2 * chi + t) * 3 + b];
-                            const cd ys = y[(2 * chi + s) * 3 + a];
-                            acc = acc + sg * (xt * conj(ys));
+#pragma unroll
+        for (int k = 0; k < 9; ++k) M[k] = cd{0, 0};
+#pragma unroll
+        for (int chi = 0; chi < 2; ++chi)
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const double sr = c_sigma[chi][p][s][t][0], si = c_sigma[chi][p][s][t][1];
+                    if (sr == 0.0 && si == 0.0) continue;
+#pragma unroll
+                    for (int b = 0; b < 3; ++b)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            const cd xt = x[(2 * chi + t) * 3 + b], ys = y[(2 * chi + s) * 3 + a];
+                            cd &m = M[b * 3 + a];
+                            // m += sigma_st xt conj(ys), sigma_st = sr (real) or i si (imaginary)
+                            if (si == 0.0) {
+                                m.r = fma(sr * xt.r, ys.r, fma(sr * xt.i, ys.i, m.r));
+                                m.i = fma(sr * xt.i, ys.r, fma(-sr * xt.r, ys.i, m.i));
+                            } else {
+                                m.r = fma(-si * xt.i, ys.r, fma(si * xt.r, ys.i, m.r));
+                                m.i = fma(si * xt.r, ys.r, fma(si * xt.i, ys.i, m.i));
+                            }
                         }
-                M[b * 3 + a] = acc;
-            }
+                }
         double2 *o = N + ((size_t)i * 6 + p) * 9;
+#pragma unroll
         for (int r = 0; r < 3; ++r)
+#pragma unroll
             for (int cc = 0; cc < 3; ++cc) {
                 const cd v = M[r * 3 + cc] + conj(M[cc * 3 + r]);
                 o[r * 3 + cc] = make_double2(v.r, v.i);
