@@ -205,6 +205,12 @@ __device__ __forceinline__ int plane_of(int a, int b)
     return lo == 0 ? hi - 1 : (lo == 1 ? hi + 1 : 5);
 }
 
+// The hopping term of g(x, mu).  1 +- gamma_mu = R P with P the spin
+// projection to a half spinor and R its reconstruction; the operator is
+// Hermitian and its upper-left block the identity, so R = P^+ and
+//   sum_s ((1 - gamma_mu) Y)_s conj(X_s) = sum_j (P Y)_j conj((P X)_j)
+// over the two spins j of the half spinors: two projections and 18 complex
+// products per term instead of a reconstruction and 36.
 template <int MU>
 __device__ void hop_force(const Geom &g, const int c[4], int i, const Spinor64 &X, const Spinor64 &Y, double kappa,
                           cd G[9])
@@ -212,23 +218,25 @@ __device__ void hop_force(const Geom &g, const int c[4], int i, const Spinor64 &
     bool wr;
     const int f = neighbour(g, c, MU, +1, &wr);
     const double sg = (MU == 3 && wr && g.tbc < 0) ? -1.0 : 1.0;
-    cd yx[12], yf[12], xx[12], xf[12], h[6], A[12], B[12];
-    Y.load(i, yx);
-    Y.load(f, yf);
-    X.load(i, xx);
-    X.load(f, xf);
-    for (int k = 0; k < 12; ++k) A[k] = B[k] = cd{0, 0};
-    project<MU, -1>(yx, h);
-    reconstruct_add<MU, -1>(A, h);  // (1 - gamma_mu) Y(x)
-    project<MU, +1>(yf, h);
-    reconstruct_add<MU, +1>(B, h);  // (1 + gamma_mu) Y(x+mu)
+    cd s[12], hy[6], hxf[6], hxx[6], hb[6];
+    Y.load(i, s);
+    project<MU, -1>(s, hy);   // P_- Y(x)
+    X.load(f, s);
+    project<MU, -1>(s, hxf);  // P_- X(x+mu)
+    X.load(i, s);
+    project<MU, +1>(s, hxx);  // P_+ X(x)
+    Y.load(f, s);
+    project<MU, +1>(s, hb);   // P_+ Y(x+mu)
     const double f2 = 2.0 * kappa * sg;
+#pragma unroll
     for (int a = 0; a < 3; ++a)
+#pragma unroll
         for (int b = 0; b < 3; ++b) {
             cd acc = {0, 0};
-            for (int s = 0; s < 4; ++s) {
-                acc = acc + A[s * 3 + a] * conj(xf[s * 3 + b]);
-                acc = acc + xx[s * 3 + a] * conj(B[s * 3 + b]);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                acc = acc + hy[j * 3 + a] * conj(hxf[j * 3 + b]);
+                acc = acc + hxx[j * 3 + a] * conj(hb[j * 3 + b]);
             }
             G[a * 3 + b] = G[a * 3 + b] + f2 * acc;
         }
