@@ -1519,6 +1519,10 @@ __device__ __forceinline__ void sap_f32_body(const Geom &g, const Spinor32 &b, c
         mbar_arrive_expect_tx(bar, lbytes);
         bulk_g2s(FL::EXPAND ? (void *)stage : (void *)sL, FL::src(U, blk, LVB), lbytes, bar);
     }
+    // a programmatic dependent of the previous colour launch (as in the FP16
+    // MR kernel): x is read only once that launch has completed
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     int lc[4], cg[4];
     local_coords(gg, l, lc);
@@ -1624,16 +1628,23 @@ __device__ __forceinline__ void sap_f32_body(const Geom &g, const Spinor32 &b, c
             rv2[2 * k + 1] = {v.z, v.w};
         }
         clover_site(Cg, i, rv2, p);
-        float pr = 0.f, pi = 0.f, pp = 0.f;
+        // <p, r> and <p, p> in four partial sums each (shorter dependent chains)
+        float sr[4] = {0.f, 0.f, 0.f, 0.f}, si[4] = {0.f, 0.f, 0.f, 0.f}, sq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
+            const int q = k & 3;
             p[k] = Cx<float>{fmaf(-kappa, acc[k].r, p[k].r), fmaf(-kappa, acc[k].i, p[k].i)};
-            pr = fmaf(p[k].r, rv2[k].r, fmaf(p[k].i, rv2[k].i, pr));
-            pi = fmaf(p[k].r, rv2[k].i, fmaf(-p[k].i, rv2[k].r, pi));
-            pp = fmaf(p[k].r, p[k].r, fmaf(p[k].i, p[k].i, pp));
+            sr[q] = fmaf(p[k].r, rv2[k].r, fmaf(p[k].i, rv2[k].i, sr[q]));
+            si[q] = fmaf(p[k].r, rv2[k].i, fmaf(-p[k].i, rv2[k].r, si[q]));
+            sq[q] = fmaf(p[k].r, p[k].r, fmaf(p[k].i, p[k].i, sq[q]));
         }
-        block_sum3(pr, pi, pp, red);
-        const Cx<float> alpha = (pp > 0.f) ? Cx<float>{pr / pp, pi / pp} : Cx<float>{0.f, 0.f};
+        float pr = (sr[0] + sr[1]) + (sr[2] + sr[3]);
+        float pi = (si[0] + si[1]) + (si[2] + si[3]);
+        float pp = (sq[0] + sq[1]) + (sq[2] + sq[3]);
+        if constexpr (VB >= 128) block_sum3_v4<VB>(pr, pi, pp, red);
+        else block_sum3(pr, pi, pp, red);
+        const float ipp = pp > 0.f ? 1.0f / pp : 0.f;
+        const Cx<float> alpha = {pr * ipp, pi * ipp};
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             e[k] = cfma(alpha, rv2[k], e[k]);
@@ -1671,10 +1682,26 @@ static int sap_run_f32(const mgc_clover_s *op, Spinor32 b, Spinor32 x, GA U, Clo
     auto kern = k_sap_f32<JAC, LVB, GA>;
     MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(g.nblocks / 2, nrhs);
+    // colour launches after the first are programmatic dependents of the one
+    // before (griddepcontrol in the kernel)
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(1 << LVB);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = pdl;
+    cfg.numAttrs = 1;
     for (int cy = 0; cy < n_cy; ++cy)
         for (int colour = 0; colour < 2; ++colour) {
             const int xz = (cy == 0 && colour == 0) ? x_is_zero : 0;
-            kern<<<grid, 1 << LVB, smem, s>>>(g, b, x, U, C, (float)op->kappa, colour, n_mr, xz, op->d_status);
+            if (cy > 0 || colour > 0)
+                MGC_CUDA(cudaLaunchKernelEx(&cfg, kern, g, b, x, U, C, (float)op->kappa, colour, n_mr, xz,
+                                            op->d_status));
+            else
+                kern<<<grid, 1 << LVB, smem, s>>>(g, b, x, U, C, (float)op->kappa, colour, n_mr, xz, op->d_status);
             count(1, sap_launch_bytes(g, 32, compress, nrhs, xz != 0));
         }
     MGC_CUDA(cudaGetLastError());
