@@ -920,6 +920,10 @@ __device__ __forceinline__ void sap_h16_body(const Geom &g, const Spinor16 &b, c
         bulk_g2s(sC, C.p + ((size_t)blk * 9 << LVB), cb, bar);
         bulk_g2s(sS, C.sc + ((size_t)blk << LVB), sb, bar);
     }
+    // a programmatic dependent of the previous colour launch (as in the MR
+    // kernel): x is read only once that launch has completed
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     int lc[4], cg[4];
     local_coords(gg, l, lc);
@@ -1376,10 +1380,9 @@ static int sap_run_h16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clo
     auto kern = JAC ? k_sap_h16<JAC, LVB, GA> : k_sap_m16<LVB, GA>;
     MGC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(g.nblocks / 2, nrhs);
-    // the MR kernel's colour launches after the first are programmatic
-    // dependents of the one before (griddepcontrol in the kernel): their
-    // blocks start, and stage their links and clover, while the previous
-    // launch's last blocks run
+    // colour launches after the first are programmatic dependents of the one
+    // before (griddepcontrol in both kernels): their blocks start, and stage
+    // their links and clover, while the previous launch's last blocks run
     cudaLaunchAttribute pdl[1];
     pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     pdl[0].val.programmaticStreamSerializationAllowed = 1;
@@ -1393,7 +1396,7 @@ static int sap_run_h16(const mgc_clover_s *op, Spinor16 b, Spinor16 x, GA U, Clo
     for (int cy = 0; cy < n_cy; ++cy)
         for (int colour = 0; colour < 2; ++colour) {
             const int xz = (cy == 0 && colour == 0) ? x_is_zero : 0;
-            if (!JAC && (cy > 0 || colour > 0))
+            if (cy > 0 || colour > 0)
                 MGC_CUDA(cudaLaunchKernelEx(&cfg, kern, g, b, x, U, C, (float)op->kappa, colour, n_mr, xz,
                                             op->d_status));
             else
