@@ -132,10 +132,45 @@ __global__ void __launch_bounds__(128) k_force_N(Geom g, Spinor64 X, Spinor64 Y,
 // with N inserted at each corner in turn (the R of the header).  With
 // E_A = N0 A + A N1, E_B = N1 B + B N2, E_C = N2 C + C N3, E_D = N3 D + D N0:
 //   R_A = E_B CD + BC E_D,  R_B = E_C DA + CD E_A,
-//   R_C = E_D AB + DA E_B,  R_D = E_A BC + AB E_C,
-// 20 matrix products for the four links against 32 one link at a time.
-// R_X goes to Rb[((p * 4 + X) * 9 + e) * V + i] (X = A, B, C, D as 0..3).
-__global__ void __launch_bounds__(128) k_force_plaq(Geom g, Gauge64 U, const double2 *N, double2 *Rb)
+//   R_C = E_D AB + DA E_B,  R_D = E_A BC + AB E_C.
+// N is Hermitian, so a link's E in one plane is shared, daggered, by its two
+// plaquettes there: with E_mu(x) = N(x) U_mu(x) + U_mu(x) N(x+mu) (k_force_E),
+// E_A = E_mu(x), E_B = E_nu(x+mu), E_C = E_mu(x+nu)^+, E_D = E_nu(x)^+.
+// 16 matrix products per plaquette for its four links (4 for the two E of
+// each site and plane, 4 pair products, 8 for the R), against 32 when each
+// link forms its own six terms.
+
+// E_mu(x) and E_nu(x) of plane p (mu < nu), to Eb[((p * 2 + k) * 9 + e) * V + i]
+// (k = 0: the link along mu, 1: along nu)
+__global__ void __launch_bounds__(128) k_force_E(Geom g, Gauge64 U, const double2 *N, double2 *Eb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const int p = blockIdx.y;
+    const int mu = p < 3 ? 0 : (p < 5 ? 1 : 2);
+    const int nu = p < 3 ? p + 1 : (p < 5 ? p - 1 : 3);
+    int c[4];
+    site_coords(g, i, c);
+    const size_t V = (size_t)g.V;
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {
+        // the link from x along d = mu (k = 0) or nu (k = 1), N at both ends
+        const int s0 = k == 0 ? 1 : 0, s1 = k == 0 ? 0 : 1;
+        cd L[9], Nm[9], E[9], T[9];
+        f_link(U, g, c, mu, 0, nu, 0, k == 0 ? mu : nu, false, L);
+        f_N(N, g, c, mu, 0, nu, 0, p, Nm);
+        f_m3mul(Nm, L, E);
+        f_N(N, g, c, mu, s0, nu, s1, p, Nm);
+        f_m3mul(L, Nm, T);
+        double2 *o = Eb + (size_t)(p * 2 + k) * 9 * V + i;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) o[e * V] = make_double2(E[e].r + T[e].r, E[e].i + T[e].i);
+    }
+}
+
+// R_A..R_D of the plaquette at x in plane p, to Rb[((p * 4 + X) * 9 + e) * V + i]
+// (X = A, B, C, D as 0..3)
+__global__ void __launch_bounds__(128) k_force_plaq(Geom g, Gauge64 U, const double2 *Eb, double2 *Rb)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.V) return;
@@ -149,6 +184,20 @@ __global__ void __launch_bounds__(128) k_force_plaq(Geom g, Gauge64 U, const dou
         double2 *o = Rb + (size_t)(p * 4 + X) * 9 * V + i;
 #pragma unroll
         for (int e = 0; e < 9; ++e) o[e * V] = make_double2(R[e].r, R[e].i);
+    };
+    // E of the link along mu (k = 0) or nu (k = 1) at x shifted by (s0, s1), daggered if dag
+    auto getE = [&](int k, int s0, int s1, bool dag, cd *E) {
+        int n[4] = {c[0], c[1], c[2], c[3]};
+        n[mu] = (n[mu] + s0) % g.L[mu];
+        n[nu] = (n[nu] + s1) % g.L[nu];
+        const double2 *q = Eb + (size_t)(p * 2 + k) * 9 * V + site_index(g, n);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const double2 v = q[(dag ? b * 3 + a : a * 3 + b) * V];
+                E[a * 3 + b] = dag ? cd{v.x, -v.y} : cd{v.x, v.y};
+            }
     };
     // the four products of neighbouring links
     cd AB[9], BC[9], CD[9], DA[9];
@@ -164,17 +213,6 @@ __global__ void __launch_bounds__(128) k_force_plaq(Geom g, Gauge64 U, const dou
         f_link(U, g, c, mu, 0, nu, 0, mu, false, X);  // A
         f_m3mul(Y, X, DA);
     }
-    // E = N_start L + L N_end for link L between the corners (d0, s0) .. (d1, s1)
-    auto edge = [&](int l0, int l1, int ldir, bool dag, int a0, int a1, int b0, int b1, cd *E) {
-        cd L[9], Nm[9], T[9];
-        f_link(U, g, c, mu, l0, nu, l1, ldir, dag, L);
-        f_N(N, g, c, mu, a0, nu, a1, p, Nm);
-        f_m3mul(Nm, L, E);
-        f_N(N, g, c, mu, b0, nu, b1, p, Nm);
-        f_m3mul(L, Nm, T);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) E[k] = E[k] + T[k];
-    };
     // R = P Q + S T
     auto two = [&](const cd *P, const cd *Q, const cd *S, const cd *T, cd *R) {
         cd W[9];
@@ -184,18 +222,18 @@ __global__ void __launch_bounds__(128) k_force_plaq(Geom g, Gauge64 U, const dou
         for (int k = 0; k < 9; ++k) R[k] = R[k] + W[k];
     };
     cd E1[9], E2[9], R[9];
-    edge(1, 0, nu, false, 1, 0, 1, 1, E1);  // E_B: B = U_nu(x+mu), corners x+mu .. x+mu+nu
-    edge(0, 0, nu, true, 0, 1, 0, 0, E2);   // E_D: D = U_nu(x)^+, corners x+nu .. x
+    getE(1, 1, 0, false, E1);  // E_B = E_nu(x+mu)
+    getE(1, 0, 0, true, E2);   // E_D = E_nu(x)^+
     two(E1, CD, BC, E2, R);
-    put(0, R);                              // R_A
+    put(0, R);                 // R_A
     two(E2, AB, DA, E1, R);
-    put(2, R);                              // R_C
-    edge(0, 0, mu, false, 0, 0, 1, 0, E1);  // E_A: A = U_mu(x), corners x .. x+mu
-    edge(0, 1, mu, true, 1, 1, 0, 1, E2);   // E_C: C = U_mu(x+nu)^+, corners x+mu+nu .. x+nu
+    put(2, R);                 // R_C
+    getE(0, 0, 0, false, E1);  // E_A = E_mu(x)
+    getE(0, 0, 1, true, E2);   // E_C = E_mu(x+nu)^+
     two(E2, DA, CD, E1, R);
-    put(1, R);                              // R_B
+    put(1, R);                 // R_B
     two(E1, BC, AB, E2, R);
-    put(3, R);                              // R_D
+    put(3, R);                 // R_D
 }
 
 __device__ __forceinline__ int plane_of(int a, int b)
@@ -369,6 +407,7 @@ int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_par
     const size_t gb = (size_t)g.V * 4 * 9 * sizeof(double2);
     double2 *phi64 = nullptr, *X = nullptr, *Y = nullptr, *T = nullptr, *N = nullptr, *stage = nullptr, *gout = nullptr;
     double2 *Rb = nullptr;  // the plaquettes' clover-leaf terms, 24 matrices per site
+    double2 *Eb = nullptr;  // the links' N L + L N per plane, 12 matrices per site
     double *part = nullptr;
     int st = MGC_OK;
     mgc_solve_params q = *p;
@@ -377,7 +416,7 @@ int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_par
     const int nb = 512;
     auto cleanup = [&]() {
         cudaFree(phi64); cudaFree(X); cudaFree(Y); cudaFree(T); cudaFree(N); cudaFree(stage); cudaFree(gout);
-        cudaFree(part); cudaFree(Rb);
+        cudaFree(part); cudaFree(Rb); cudaFree(Eb);
     };
 #define FTRY(call)                         \
     do {                                   \
@@ -395,6 +434,7 @@ int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_par
     FCUDA(cudaMalloc(&T, vb));
     FCUDA(cudaMalloc(&N, (size_t)g.V * 54 * sizeof(double2)));
     FCUDA(cudaMalloc(&Rb, (size_t)g.V * 24 * 9 * sizeof(double2)));
+    FCUDA(cudaMalloc(&Eb, (size_t)g.V * 12 * 9 * sizeof(double2)));
     FCUDA(cudaMalloc(&part, 4 * nb * sizeof(double)));
     if (!p->on_device) {
         FCUDA(cudaMalloc(&stage, vb));
@@ -443,9 +483,12 @@ int force(mgc_clover_s *op, const double *phi, double *dSdU, const mgc_solve_par
     k_force_N<<<grid_for(g.V, 128), 128, 0, s>>>(g, Spinor64{X, g.lvb}, Spinor64{Y, g.lvb}, N);
     FCUDA(cudaGetLastError());
     count(1, (double)g.V * (2 * 192.0 + 54 * 16.0));
-    k_force_plaq<<<dim3(grid_for(g.V, 128), 6), 128, 0, s>>>(g, Gauge64{op->gauge->U64, g.lvb}, N, Rb);
+    k_force_E<<<dim3(grid_for(g.V, 128), 6), 128, 0, s>>>(g, Gauge64{op->gauge->U64, g.lvb}, N, Eb);
     FCUDA(cudaGetLastError());
-    count(1, (double)g.V * (576.0 + 54 * 16.0 + 24 * 144.0));
+    count(1, (double)g.V * (576.0 + 54 * 16.0 + 12 * 144.0));
+    k_force_plaq<<<dim3(grid_for(g.V, 128), 6), 128, 0, s>>>(g, Gauge64{op->gauge->U64, g.lvb}, Eb, Rb);
+    FCUDA(cudaGetLastError());
+    count(1, (double)g.V * (576.0 + 12 * 144.0 + 24 * 144.0));
     double2 *dst = p->on_device ? (double2 *)dSdU : gout;
     dim3 grid(grid_for(g.V, 128), 4);
     k_force<<<grid, 128, 0, s>>>(g, Gauge64{op->gauge->U64, g.lvb}, Spinor64{X, g.lvb}, Spinor64{Y, g.lvb}, Rb,
