@@ -43,6 +43,20 @@ __device__ __forceinline__ void f_m3mul(const cd *a, const cd *b, cd *o)
     for (int k = 0; k < 9; ++k) o[k] = t[k];
 }
 
+// o += a b: the product's multiply-adds accumulate onto o (o distinct from a, b)
+__device__ __forceinline__ void f_m3mul_acc(const cd *a, const cd *b, cd *o)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cd acc = cfma(a[i * 3], b[j], o[i * 3 + j]);
+            acc = cfma(a[i * 3 + 1], b[3 + j], acc);
+            acc = cfma(a[i * 3 + 2], b[6 + j], acc);
+            o[i * 3 + j] = acc;
+        }
+}
+
 __device__ __forceinline__ void f_link(const Gauge64 &U, const Geom &g, const int c[4], int d0, int s0, int d1, int s1,
                                        int dir, bool dag, cd *o)
 {
@@ -156,15 +170,15 @@ __global__ void __launch_bounds__(128) k_force_E(Geom g, Gauge64 U, const double
     for (int k = 0; k < 2; ++k) {
         // the link from x along d = mu (k = 0) or nu (k = 1), N at both ends
         const int s0 = k == 0 ? 1 : 0, s1 = k == 0 ? 0 : 1;
-        cd L[9], Nm[9], E[9], T[9];
+        cd L[9], Nm[9], E[9];
         f_link(U, g, c, mu, 0, nu, 0, k == 0 ? mu : nu, false, L);
         f_N(N, g, c, mu, 0, nu, 0, p, Nm);
         f_m3mul(Nm, L, E);
         f_N(N, g, c, mu, s0, nu, s1, p, Nm);
-        f_m3mul(L, Nm, T);
+        f_m3mul_acc(L, Nm, E);
         double2 *o = Eb + (size_t)(p * 2 + k) * 9 * V + i;
 #pragma unroll
-        for (int e = 0; e < 9; ++e) o[e * V] = make_double2(E[e].r + T[e].r, E[e].i + T[e].i);
+        for (int e = 0; e < 9; ++e) o[e * V] = make_double2(E[e].r, E[e].i);
     }
 }
 
@@ -215,11 +229,8 @@ __global__ void __launch_bounds__(128) k_force_plaq(Geom g, Gauge64 U, const dou
     }
     // R = P Q + S T
     auto two = [&](const cd *P, const cd *Q, const cd *S, const cd *T, cd *R) {
-        cd W[9];
         f_m3mul(P, Q, R);
-        f_m3mul(S, T, W);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) R[k] = R[k] + W[k];
+        f_m3mul_acc(S, T, R);
     };
     cd E1[9], E2[9], R[9];
     getE(1, 1, 0, false, E1);  // E_B = E_nu(x+mu)
@@ -266,6 +277,11 @@ __device__ void hop_force(const Geom &g, const int c[4], int i, const Spinor64 &
     Y.load(f, s);
     project<MU, +1>(s, hb);   // P_+ Y(x+mu)
     const double f2 = 2.0 * kappa * sg;
+    // acc += u conj(v) as multiply-adds
+    auto macc = [](cd &acc, cd u, cd v) {
+        acc.r = fma(u.r, v.r, fma(u.i, v.i, acc.r));
+        acc.i = fma(u.i, v.r, fma(-u.r, v.i, acc.i));
+    };
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -273,10 +289,10 @@ __device__ void hop_force(const Geom &g, const int c[4], int i, const Spinor64 &
             cd acc = {0, 0};
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                acc = acc + hy[j * 3 + a] * conj(hxf[j * 3 + b]);
-                acc = acc + hxx[j * 3 + a] * conj(hb[j * 3 + b]);
+                macc(acc, hy[j * 3 + a], hxf[j * 3 + b]);
+                macc(acc, hxx[j * 3 + a], hb[j * 3 + b]);
             }
-            G[a * 3 + b] = G[a * 3 + b] + f2 * acc;
+            G[a * 3 + b] = cd{fma(f2, acc.r, G[a * 3 + b].r), fma(f2, acc.i, G[a * 3 + b].i)};
         }
 }
 
@@ -300,8 +316,9 @@ __global__ void k_force(Geom g, Gauge64 U, Spinor64 X, Spinor64 Y, const double2
     else if (mu == 2) hop_force<2>(g, c, i, X, Y, kappa, G);
     else hop_force<3>(g, c, i, X, Y, kappa, G);
 
-    const cd cp = {0.0, -kappa * csw / 4.0};  // c'
-    const cd cpc = conj(cp);
+    // c' = -i kc with kc = kappa c_SW / 4: conj(c') R^+ adds kc (Im, Re) of
+    // R's transpose, c' R adds kc (Im R, -Re R)
+    const double kc = kappa * csw / 4.0;
     const size_t V = (size_t)g.V;
     auto get = [&](int p, int Xr, int site, cd *R) {
         const double2 *q = Rb + (size_t)(p * 4 + Xr) * 9 * V + site;
@@ -321,12 +338,18 @@ __global__ void k_force(Geom g, Gauge64 U, Spinor64 X, Spinor64 Y, const double2
         // undaggered: A of the plaquette at x (mu < s) or B of the one at x - s (s < mu)
         if (mu < sgm) get(p, 0, i, R);
         else get(p, 1, back, R);
+#pragma unroll
         for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) G[a * 3 + b] = G[a * 3 + b] + cpc * conj(R[b * 3 + a]);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const cd r = R[b * 3 + a];
+                G[a * 3 + b] = cd{fma(kc, r.i, G[a * 3 + b].r), fma(kc, r.r, G[a * 3 + b].i)};
+            }
         // daggered: C of the plaquette at x - s (mu < s) or D of the one at x (s < mu)
         if (mu < sgm) get(p, 2, back, R);
         else get(p, 3, i, R);
-        for (int k = 0; k < 9; ++k) G[k] = G[k] + cp * R[k];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) G[k] = cd{fma(kc, R[k].i, G[k].r), fma(-kc, R[k].r, G[k].i)};
     }
     double2 *o = out + (canon_index(g, c) * 4 + mu) * 9;
     for (int k = 0; k < 9; ++k) o[k] = make_double2(G[k].r, G[k].i);
