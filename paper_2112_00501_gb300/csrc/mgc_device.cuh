@@ -9,6 +9,7 @@
 // shifts and masks.
 #pragma once
 
+#include <cfloat>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -257,7 +258,7 @@ struct Spinor16 {
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(s[k].r), fabsf(s[k].i)));
-        const float inv = (m > 0.f) ? 1.0f / m : 0.f;
+        const float inv = (m >= FLT_MIN) ? 1.0f / m : 0.f;  // a site below FP32's normal range is stored as zero
         uint4 *q = const_cast<uint4 *>(at(i));
 #pragma unroll
         for (int k = 0; k < 3; ++k) {

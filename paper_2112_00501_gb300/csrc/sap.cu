@@ -1155,7 +1155,8 @@ __device__ __forceinline__ void m16_store_r(uint4 *r16, float *rsc, int l, const
 #pragma unroll
     for (int k = 0; k < 3; ++k) t[k] = fmaxf(t[k], t[k + 3]);
     const float m = fmaxf(fmaxf(t[0], t[1]), t[2]);
-    const float inv = m > 0.f ? 1.0f / m : 0.f;
+    // below FP32's normal range the site is stored as zero (1/m would overflow)
+    const float inv = m >= FLT_MIN ? 1.0f / m : 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
         r16[k * VB + l] = make_uint4(pack_half2(rr[4 * k] * inv, ri[4 * k] * inv),
@@ -1337,7 +1338,9 @@ __device__ __forceinline__ void sap_m16_body(const Geom &g, const Spinor16 &b, c
         float pp = (sp[0] + sp[1]) + (sp[2] + sp[3]);
         if constexpr (VB >= 128) block_sum3_v4<VB>(pr, pi, pp, red);
         else block_sum3(pr, pi, pp, red);
-        const float ipp = pp > 0.f ? 1.0f / pp : 0.f;
+        // a domain whose <p, p> is below FP32's normal range takes no step
+        // (1 / <p, p> would overflow)
+        const float ipp = pp >= FLT_MIN ? 1.0f / pp : 0.f;
         const float alr = pr * ipp, ali = pi * ipp;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -1646,7 +1649,9 @@ __device__ __forceinline__ void sap_f32_body(const Geom &g, const Spinor32 &b, c
         float pp = (sq[0] + sq[1]) + (sq[2] + sq[3]);
         if constexpr (VB >= 128) block_sum3_v4<VB>(pr, pi, pp, red);
         else block_sum3(pr, pi, pp, red);
-        const float ipp = pp > 0.f ? 1.0f / pp : 0.f;
+        // a domain whose <p, p> is below FP32's normal range takes no step
+        // (1 / <p, p> would overflow)
+        const float ipp = pp >= FLT_MIN ? 1.0f / pp : 0.f;
         const Cx<float> alpha = {pr * ipp, pi * ipp};
 #pragma unroll
         for (int k = 0; k < 12; ++k) {

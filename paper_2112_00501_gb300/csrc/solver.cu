@@ -1152,15 +1152,19 @@ static int inner_fgcr32(mgc_clover_s *op, const mgc_solve_params *p, double tol_
     return MGC_OK;
 }
 
-// r32 = b - t site by site (the FP64 and FP32 packed layouts differ; t may be
-// null: r32 = b), its FP16 copy into rl when rl is given (the FP16 smoother's
-// input), and ||b - t||^2 into a device scalar slot.  The FP64
-// residual itself is not kept: the inner solve only needs its FP32 copy, and
-// r32 is not normalised, since FP32 covers every residual this solve reaches
-// (down to tol ||b||).
-static int residual_to32(mgc_clover_s *op, const double2 *b, const double2 *t, float2 *r32, void *rl, int slot,
-                         cudaStream_t s)
+// r32 = scale (b - t) site by site (the FP64 and FP32 packed layouts differ;
+// t may be null: r32 = scale b), its FP16 copy into rl when rl is given (the
+// FP16 smoother's input), and the unscaled ||b - t||^2 into a device scalar
+// slot.  The FP64 residual itself is not kept: the inner solve only needs its
+// FP32 copy.
+static int residual_to32(mgc_clover_s *op, const double2 *b, const double2 *t, float2 *r32, void *rl, double scale,
+                         int slot, cudaStream_t s)
 {
+    // scale (a power of two) is applied after the conversion to FP32, where
+    // the product is exact and costs no FP64 instruction, unless it is so far
+    // from 1 that the unscaled values could leave FP32's range
+    const bool wide = scale > 0x1p90 || scale < 0x1p-90;
+    const float sf = (float)scale;
     SolverWork *W = op->work;
     const Geom g = op->gauge->lat->g;
     const Spinor64 B{const_cast<double2 *>(b), g.lvb}, T{const_cast<double2 *>(t), g.lvb};
@@ -1178,9 +1182,13 @@ static int residual_to32(mgc_clover_s *op, const double2 *b, const double2 *t, f
             for (int k = 0; k < 12; ++k) v[k] = v[k] - u[k];
         }
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            w[k] = Cx<float>{(float)v[k].r, (float)v[k].i};
-            acc[0] = fma(v[k].r, v[k].r, fma(v[k].i, v[k].i, acc[0]));
+        for (int k = 0; k < 12; ++k) acc[0] = fma(v[k].r, v[k].r, fma(v[k].i, v[k].i, acc[0]));
+        if (wide) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) w[k] = Cx<float>{(float)(scale * v[k].r), (float)(scale * v[k].i)};
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) w[k] = Cx<float>{(float)v[k].r * sf, (float)v[k].i * sf};
         }
         R.store((int)i, w);
         if (has_l) RL.store((int)i, w);
@@ -1191,9 +1199,10 @@ static int residual_to32(mgc_clover_s *op, const double2 *b, const double2 *t, f
     return MGC_OK;
 }
 
-// x += sum_j gamma_j z_j site by site: the sum in FP32 (its rounding is far
+// x += es sum_j gamma_j z_j site by site: the sum in FP32 (its rounding is far
 // below the inner tolerance), the update of x in FP64
-static int axpy_sum32(mgc_clover_s *op, double2 *x, const PtrList4 &Lz, const CoefList &G, int k, cudaStream_t s)
+static int axpy_sum32(mgc_clover_s *op, double2 *x, const PtrList4 &Lz, const CoefList &G, int k, double es,
+                      cudaStream_t s)
 {
     const Geom g = op->gauge->lat->g;
     const Spinor64 X{x, g.lvb};
@@ -1215,7 +1224,7 @@ static int axpy_sum32(mgc_clover_s *op, double2 *x, const PtrList4 &Lz, const Co
         Cx<double> v[12];
         X.load((int)i, v);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) v[c] = v[c] + Cx<double>{(double)e[c].r, (double)e[c].i};
+        for (int c = 0; c < 12; ++c) v[c] = Cx<double>{fma(es, (double)e[c].r, v[c].r), fma(es, (double)e[c].i, v[c].i)};
         X.store((int)i, v);
     };
     k_map<<<red_grid(g.V), RT, 0, s>>>((long long)g.V, f);
@@ -1224,11 +1233,12 @@ static int axpy_sum32(mgc_clover_s *op, double2 *x, const PtrList4 &Lz, const Co
     return MGC_OK;
 }
 
-// x += sum_j gamma_j z_j for FP16 z_j (the FP16-smoother path), as axpy_sum32
+// x += es sum_j gamma_j z_j for FP16 z_j (the FP16-smoother path), as axpy_sum32
 struct Spinor16List {
     Spinor16 z[MAXM];
 };
-static int axpy_sum16(mgc_clover_s *op, double2 *x, const Spinor16List &Z, const CoefList &G, int k, cudaStream_t s)
+static int axpy_sum16(mgc_clover_s *op, double2 *x, const Spinor16List &Z, const CoefList &G, int k, double es,
+                      cudaStream_t s)
 {
     const Geom g = op->gauge->lat->g;
     const Spinor64 X{x, g.lvb};
@@ -1248,13 +1258,27 @@ static int axpy_sum16(mgc_clover_s *op, double2 *x, const Spinor16List &Z, const
         Cx<double> v[12];
         X.load((int)i, v);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) v[c] = v[c] + Cx<double>{(double)e[c].r, (double)e[c].i};
+        for (int c = 0; c < 12; ++c) v[c] = Cx<double>{fma(es, (double)e[c].r, v[c].r), fma(es, (double)e[c].i, v[c].i)};
         X.store((int)i, v);
     };
     k_map<<<red_grid(g.V), RT, 0, s>>>((long long)g.V, f);
     MGC_CUDA(cudaGetLastError());
     count(1, (double)g.V * (2 * 192.0 + 52.0 * k));
     return MGC_OK;
+}
+
+// The power of two nearest 1 / (the rms of the 2n real components of a vector
+// whose squared norm is rr): the inner solve works on the residual times this
+// scale.  Scaling by a power of two is exact and commutes with every rounding,
+// so the inner solve's results are those of the unscaled residual wherever
+// that stays in FP32's normal range, and it keeps FP32's sums of squares in
+// range for sources of any magnitude and residuals at any depth.
+static double unit_scale(double rr, long long n)
+{
+    if (!(rr > 0.0) || !std::isfinite(rr)) return 1.0;
+    int e = 0;
+    std::frexp(std::sqrt(rr / (2.0 * (double)n)), &e);
+    return std::ldexp(1.0, -e);
 }
 
 static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
@@ -1266,6 +1290,7 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
     void *rl = fp16_directions(p) ? W->rl : nullptr;  // the FP16 smoother's input
     double *sc = W->scal;
     double bb, rr;
+    double rs = 1.0;  // r32 (and its FP16 copy) = rs (b - D x), rs a power of two
     info->iters = 0;
     info->restarts = 0;
     info->true_res = 0;
@@ -1277,15 +1302,25 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
             return MGC_OK;
         }
         MGC_TRY(apply_D64(op, x, t, s));
-        MGC_TRY(residual_to32(op, b, t, r32, rl, S_RR, s));
+        MGC_TRY(residual_to32(op, b, t, r32, rl, rs, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
     } else {
         // x = 0: r = b, and ||b||^2 from the same pass
         MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
-        MGC_TRY(residual_to32(op, b, nullptr, r32, rl, S_RR, s));
+        MGC_TRY(residual_to32(op, b, nullptr, r32, rl, rs, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
         bb = rr;
         if (bb == 0.0) return MGC_OK;
+    }
+    // a first residual far from unit rms (beyond 2^+-30) is written again at
+    // its unit scale; later ones are written at the unit scale of the inner
+    // solve's final residual, the prediction of theirs
+    if (std::isfinite(rr) && rr > 0.0) {
+        const double u = unit_scale(rr, n);
+        if (u > 0x1p30 || u < 0x1p-30) {
+            rs = u;
+            MGC_TRY(residual_to32(op, b, p->x_is_guess ? t : nullptr, r32, rl, rs, S_RR, s));
+        }
     }
     const double tol2 = p->tol * p->tol * bb;
     int iters = 0;
@@ -1301,7 +1336,7 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
         int k = 0;
         double rri;
         std::vector<zd> gamma;
-        MGC_TRY(inner_fgcr32(op, p, tin, rr, p->max_iter - iters, &k, gamma, &rri, s));
+        MGC_TRY(inner_fgcr32(op, p, tin, rr * rs * rs, p->max_iter - iters, &k, gamma, &rri, s));
         iters += k;
         // x += e, e = sum_j gamma_j z_j
         CoefList G{};
@@ -1309,17 +1344,18 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
         if (rl) {
             Spinor16List Z{};
             for (int j = 0; j < k; ++j) Z.z[j] = view16(op->gauge->lat->g, W->z16[j]);
-            MGC_TRY(axpy_sum16(op, x, Z, G, k, s));
+            MGC_TRY(axpy_sum16(op, x, Z, G, k, 1.0 / rs, s));
         } else {
             PtrList4 Lz{};
             for (int j = 0; j < k; ++j) Lz.p[j] = (const float4 *)W->z32[j];
-            MGC_TRY(axpy_sum32(op, x, Lz, G, k, s));
+            MGC_TRY(axpy_sum32(op, x, Lz, G, k, 1.0 / rs, s));
         }
         // the inner solve predicts that this x meets the tolerance: it goes to
         // the host (host-pointer solves) while the FP64 residual checks it
-        if (W->host_x && rri <= tol2) MGC_TRY(copy_x_early(op, s));
+        if (W->host_x && rri <= tol2 * rs * rs) MGC_TRY(copy_x_early(op, s));
         MGC_TRY(apply_D64(op, x, t, s));
-        MGC_TRY(residual_to32(op, b, t, r32, rl, S_RR, s));
+        if (rri > 0.0 && std::isfinite(rri)) rs = unit_scale(rri / (rs * rs), n);
+        MGC_TRY(residual_to32(op, b, t, r32, rl, rs, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
         if (!(rr <= tol2)) MGC_TRY(join_copy(W, s));  // x changes again
         info->iters = iters;
@@ -1542,12 +1578,49 @@ static int check_params(const mgc_clover_s *op, const mgc_solve_params *p)
     return MGC_OK;
 }
 
+// The FP64 Krylov methods hand their vectors to an FP32 or FP16 smoother as
+// they are.  For a source whose rms per real component lies beyond 2^+-30 they
+// solve D (u x) = u b instead, u the power of two that brings that rms near 1
+// (exact scaling: b and the guess are scaled in place, x back at the end), so
+// that the smoother's sums of squares stay in FP32's range.  The two-level
+// and QWS solves scale the residual of each outer step instead.
 static int run_method(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
 {
-    if (p->method == 0) return fgcr(op, p, info, s);
-    if (p->method == 1) return fbicgstab(op, p, info, s);
     if (p->method == 3) return qws(op, p, info, s);
-    return two_level(op, p, info, s);
+    if (p->method == 2) return two_level(op, p, info, s);
+    SolverWork *W = op->work;
+    const long long n = (long long)op->gauge->lat->g.V * 12;
+    double2 *x = W->x, *b = W->b;
+    double u = 1.0;
+    if (p->precond && p->smoother_prec != 64) {
+        MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, b[e]); }, W, W->scal + S_BB, s, 1));
+        double bb = 0.0;
+        MGC_TRY(read_scalar(W, S_BB, &bb, s));
+        const double v = unit_scale(bb, n);
+        if (v > 0x1p30 || v < 0x1p-30) {
+            u = v;
+            const bool guess = p->x_is_guess != 0;
+            MGC_TRY(map(
+                n,
+                [=] __device__(long long e) {
+                    b[e] = make_double2(u * b[e].x, u * b[e].y);
+                    if (guess) x[e] = make_double2(u * x[e].x, u * x[e].y);
+                },
+                s, guess ? 4 : 2));
+        }
+    }
+    const int st = p->method == 0 ? fgcr(op, p, info, s) : fbicgstab(op, p, info, s);
+    if (u != 1.0) {
+        const double iu = 1.0 / u;
+        MGC_TRY(map(
+            n,
+            [=] __device__(long long e) {
+                x[e] = make_double2(iu * x[e].x, iu * x[e].y);
+                b[e] = make_double2(iu * b[e].x, iu * b[e].y);
+            },
+            s, 4));
+    }
+    return st;
 }
 
 // ------------------------------------------------------------------ solve without allocation

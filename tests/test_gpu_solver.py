@@ -51,6 +51,25 @@ def test_solve_reaches_1e10(name, method, smoother, compress):
     assert rel(xr, xo) < 1e-8
 
 
+@pytest.mark.parametrize("method,smoother,compress", [(0, 16, 12), (1, 32, 18), (2, 16, 12), (2, 32, 18), (3, 16, 12)])
+@pytest.mark.parametrize("k", [-120, 120])
+def test_solve_is_scale_invariant(method, smoother, compress, k):
+    """D x = b is linear: a source scaled by 2^k (rms per component near 1e-36
+    or 1e+36, so that sums of squares leave FP32's range) gives x scaled by
+    2^k, with the true residual still <= 1e-10."""
+    name = "mid_8^4"
+    dims, block, eps, kappa, csw, U, psi = fields(name)
+    op = _op(name, smoother, compress)
+    f = 2.0 ** k
+    x1, i1 = op.solve(torch.from_numpy(psi).cuda(), method=method, smoother_prec=smoother, tol=1e-10)
+    xk, ik = op.solve(torch.from_numpy(psi * f).cuda(), method=method, smoother_prec=smoother, tol=1e-10)
+    assert i1.status == 0 and ik.status == 0
+    assert ik.true_res <= 1e-10
+    xs = xk.cpu().numpy() / f
+    assert _oracle_residual(name, xs) <= 1e-10
+    assert rel(xs, x1.cpu().numpy()) < 1e-8
+
+
 def test_unpreconditioned_and_host_pointer_paths():
     name = "c0_4^4"
     dims, block, eps, kappa, csw, U, psi = fields(name)
