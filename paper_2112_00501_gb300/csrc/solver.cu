@@ -719,8 +719,9 @@ int mg_solve(mgc_mg_s *M, const double *b, double *x, const mgc_solve_params *p,
 // FP64 defect correction (the double-precision Richardson iteration around a
 // single-precision solver of Sec. 2) with an FP32 inner FGCR(m) preconditioned
 // by SAP:  r = b - D x in FP64;  solve D e = r to inner_tol ||r|| with FP32
-// vectors and the FP32 operator (r enters as its unnormalised FP32 copy);
-// x += e in FP64;  repeat until the FP64 true residual meets tol.  Inner
+// vectors and the FP32 operator (r enters as its FP32 copy times a power of
+// two s, see unit_scale); x += e / s in FP64;  repeat until the FP64 true
+// residual meets tol.  Inner
 // products of the FP32 vectors accumulate in FP32 over chunks of entries per
 // thread and in FP64 beyond that; the Gram-Schmidt coefficients and step
 // lengths are FP64 host scalars.  The inner
