@@ -568,7 +568,8 @@ def bench_force(lib, stream, prec=None, compress=None):
 
 def profile_kernel(which):
     """A few launches of one kernel on 24^3 x 48 at the workload's storage format
-    (working set above the L2 size, about 2 GB on the device), for ncu."""
+    (working set above the L2 size, about 2 GB on the device), for ncu; `force`:
+    one link-force evaluation on 16^4 (its FP64 fields about 0.5 GB)."""
     import torch
 
     import __graft_entry__
@@ -576,6 +577,19 @@ def profile_kernel(which):
     __graft_entry__.build()
     from paper_2112_00501_gb300 import api, synth
 
+    if which == "force":
+        fw = FORCE_WORKLOAD
+        fdims = (16, 16, 16, 16)
+        Uf = synth.gauge_field(fdims, fw["eps"], synth.gauge_seed(fw["config_index"]))
+        phi = torch.from_numpy(synth.gaussian_spinor(fdims, synth.source_seed(fw["config_index"]))).cuda()
+        lat = api.Lattice(fdims, fw["block"], -1)
+        op = api.CloverOperator(api.Gauge(lat, torch.from_numpy(Uf).cuda(), storage_prec=fw["prec"],
+                                          compress=fw["compress"]), fw["kappa"], fw["csw"])
+        params = api.solve_params(method=2, precond=1, smoother_prec=fw["prec"], tol=1e-10, max_iter=500)
+        op.force(phi, params)
+        torch.cuda.synchronize()
+        print("profile run done")
+        return 0
     if which in ("dslash_batch", "sap_batch"):
         # the batched workload (12 + 8 + 8 right-hand sides on three lattices), its
         # autotuned operator launch or one smoother sweep over the batch
@@ -644,9 +658,9 @@ def main():
     ap.add_argument("--no-mg", action="store_true")
     ap.add_argument("--no-c1", action="store_true")
     ap.add_argument("--profile-kernel", choices=["sap", "sap32", "dslash", "dslash32", "dslash16x18", "dslash64",
-                                                 "dslash_batch", "sap_batch"],
+                                                 "dslash_batch", "sap_batch", "force"],
                     default=None,
-                    help="run only a few launches of one kernel on 24^3x48 (for ncu captures)")
+                    help="run only a few launches of one kernel (for ncu captures)")
     args = ap.parse_args()
     if args.profile_kernel:
         return profile_kernel(args.profile_kernel)
