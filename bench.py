@@ -40,9 +40,9 @@ CPU_SAMPLE_DIMS = (16, 16, 16, 8)
 # the rate mgc_fma_peak measures in the run, which is the roofline's peak
 FP32_FMA_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of one k_sap_m16 colour launch per lattice site,
-# from an ncu capture on 24^3 x 48 (155,394,560 + 8,755,200 B over 663,552
+# from an ncu capture on 24^3 x 48 (155,398,144 + 8,841,728 B over 663,552
 # sites); the kernel's traffic is per domain, so it scales with the sites
-SAP_DRAM_BYTES_PER_SITE = (155394560.0 + 8755200.0) / 663552
+SAP_DRAM_BYTES_PER_SITE = (155398144.0 + 8841728.0) / 663552
 # conventional flop counts per site: hopping 1320, clover 504, kappa axpy 48
 FLOP_D = 1872.0
 
