@@ -269,10 +269,11 @@ void mgc_solve_params_default(mgc_solve_params *p);
  * of 3 keep their vectors, inner products, orthogonalisation and residual
  * updates in FP64; method 2 keeps its residual, x and norms in FP64 and runs
  * its inner solve in FP32 (above); the SAP preconditioner in smoother_prec.
- * The solve is scale invariant over FP64's range: method 2 hands its inner
- * solve each outer residual multiplied by a power of two that brings its rms
- * near 1, methods 0 and 1 solve D (u x) = u b for a source whose rms lies
- * beyond 2^+-30 (u a power of two), method 3 normalises its inner source.
+ * The solve is scale invariant for every source whose squared norm is a
+ * normal FP64 number: method 2 hands its inner solve each outer residual
+ * multiplied by a power of two that brings its rms near 1, methods 0 and 1
+ * solve D (u x) = u b for a source whose rms lies beyond 2^+-30 (u a power
+ * of two), method 3 normalises its inner source.
  * Synchronises stream.
  * Host pointers (on_device = 0): with x in page-locked memory, method 2
  * copies x back on a stream of its own while the FP64 residual that confirms

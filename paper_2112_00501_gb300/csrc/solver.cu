@@ -720,7 +720,7 @@ int mg_solve(mgc_mg_s *M, const double *b, double *x, const mgc_solve_params *p,
 // single-precision solver of Sec. 2) with an FP32 inner FGCR(m) preconditioned
 // by SAP:  r = b - D x in FP64;  solve D e = r to inner_tol ||r|| with FP32
 // vectors and the FP32 operator (r enters as its FP32 copy times a power of
-// two s, see unit_scale); x += e / s in FP64;  repeat until the FP64 true
+// two 2^k, see unit_exp); x += 2^-k e in FP64;  repeat until the FP64 true
 // residual meets tol.  Inner
 // products of the FP32 vectors accumulate in FP32 over chunks of entries per
 // thread and in FP64 beyond that; the Gram-Schmidt coefficients and step
@@ -1268,18 +1268,20 @@ static int axpy_sum16(mgc_clover_s *op, double2 *x, const Spinor16List &Z, const
     return MGC_OK;
 }
 
-// The power of two nearest 1 / (the rms of the 2n real components of a vector
-// whose squared norm is rr): the inner solve works on the residual times this
-// scale.  Scaling by a power of two is exact and commutes with every rounding,
-// so the inner solve's results are those of the unscaled residual wherever
-// that stays in FP32's normal range, and it keeps FP32's sums of squares in
-// range for sources of any magnitude and residuals at any depth.
-static double unit_scale(double rr, long long n)
+// The exponent of the power of two nearest 1 / (the rms of the 2n real
+// components of a vector whose squared norm is rr): the inner solve works on
+// the residual times 2^e.  Scaling by a power of two is exact and commutes
+// with every rounding, so the inner solve's results are those of the
+// unscaled residual wherever that stays in FP32's normal range, and it keeps
+// FP32's sums of squares in range for any residual whose squared norm is a
+// normal FP64 number.  Scaled norms are formed with ldexp, never by
+// multiplying with 2^e twice (which would overflow for the smallest ones).
+static int unit_exp(double rr, long long n)
 {
-    if (!(rr > 0.0) || !std::isfinite(rr)) return 1.0;
+    if (!(rr > 0.0) || !std::isfinite(rr)) return 0;
     int e = 0;
     std::frexp(std::sqrt(rr / (2.0 * (double)n)), &e);
-    return std::ldexp(1.0, -e);
+    return -e;
 }
 
 static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info *info, cudaStream_t s)
@@ -1291,7 +1293,7 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
     void *rl = fp16_directions(p) ? W->rl : nullptr;  // the FP16 smoother's input
     double *sc = W->scal;
     double bb, rr;
-    double rs = 1.0;  // r32 (and its FP16 copy) = rs (b - D x), rs a power of two
+    int re = 0;  // r32 (and its FP16 copy) = 2^re (b - D x)
     info->iters = 0;
     info->restarts = 0;
     info->true_res = 0;
@@ -1303,12 +1305,12 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
             return MGC_OK;
         }
         MGC_TRY(apply_D64(op, x, t, s));
-        MGC_TRY(residual_to32(op, b, t, r32, rl, rs, S_RR, s));
+        MGC_TRY(residual_to32(op, b, t, r32, rl, 1.0, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
     } else {
         // x = 0: r = b, and ||b||^2 from the same pass
         MGC_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
-        MGC_TRY(residual_to32(op, b, nullptr, r32, rl, rs, S_RR, s));
+        MGC_TRY(residual_to32(op, b, nullptr, r32, rl, 1.0, S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
         bb = rr;
         if (bb == 0.0) return MGC_OK;
@@ -1317,10 +1319,10 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
     // its unit scale; later ones are written at the unit scale of the inner
     // solve's final residual, the prediction of theirs
     if (std::isfinite(rr) && rr > 0.0) {
-        const double u = unit_scale(rr, n);
-        if (u > 0x1p30 || u < 0x1p-30) {
-            rs = u;
-            MGC_TRY(residual_to32(op, b, p->x_is_guess ? t : nullptr, r32, rl, rs, S_RR, s));
+        const int e = unit_exp(rr, n);
+        if (e > 30 || e < -30) {
+            re = e;
+            MGC_TRY(residual_to32(op, b, p->x_is_guess ? t : nullptr, r32, rl, std::ldexp(1.0, re), S_RR, s));
         }
     }
     const double tol2 = p->tol * p->tol * bb;
@@ -1337,7 +1339,7 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
         int k = 0;
         double rri;
         std::vector<zd> gamma;
-        MGC_TRY(inner_fgcr32(op, p, tin, rr * rs * rs, p->max_iter - iters, &k, gamma, &rri, s));
+        MGC_TRY(inner_fgcr32(op, p, tin, std::ldexp(rr, 2 * re), p->max_iter - iters, &k, gamma, &rri, s));
         iters += k;
         // x += e, e = sum_j gamma_j z_j
         CoefList G{};
@@ -1345,18 +1347,18 @@ static int two_level(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_info
         if (rl) {
             Spinor16List Z{};
             for (int j = 0; j < k; ++j) Z.z[j] = view16(op->gauge->lat->g, W->z16[j]);
-            MGC_TRY(axpy_sum16(op, x, Z, G, k, 1.0 / rs, s));
+            MGC_TRY(axpy_sum16(op, x, Z, G, k, std::ldexp(1.0, -re), s));
         } else {
             PtrList4 Lz{};
             for (int j = 0; j < k; ++j) Lz.p[j] = (const float4 *)W->z32[j];
-            MGC_TRY(axpy_sum32(op, x, Lz, G, k, 1.0 / rs, s));
+            MGC_TRY(axpy_sum32(op, x, Lz, G, k, std::ldexp(1.0, -re), s));
         }
         // the inner solve predicts that this x meets the tolerance: it goes to
         // the host (host-pointer solves) while the FP64 residual checks it
-        if (W->host_x && rri <= tol2 * rs * rs) MGC_TRY(copy_x_early(op, s));
+        if (W->host_x && std::ldexp(rri, -2 * re) <= tol2) MGC_TRY(copy_x_early(op, s));
         MGC_TRY(apply_D64(op, x, t, s));
-        if (rri > 0.0 && std::isfinite(rri)) rs = unit_scale(rri / (rs * rs), n);
-        MGC_TRY(residual_to32(op, b, t, r32, rl, rs, S_RR, s));
+        if (rri > 0.0 && std::isfinite(rri)) re = unit_exp(std::ldexp(rri, -2 * re), n);
+        MGC_TRY(residual_to32(op, b, t, r32, rl, std::ldexp(1.0, re), S_RR, s));
         MGC_TRY(read_scalar(W, S_RR, &rr, s));
         if (!(rr <= tol2)) MGC_TRY(join_copy(W, s));  // x changes again
         info->iters = iters;
@@ -1597,9 +1599,9 @@ static int run_method(mgc_clover_s *op, const mgc_solve_params *p, mgc_solve_inf
         MGC_TRY(reduce<1>(n, [=] __device__(long long e, double *acc) { acc_n2(acc, b[e]); }, W, W->scal + S_BB, s, 1));
         double bb = 0.0;
         MGC_TRY(read_scalar(W, S_BB, &bb, s));
-        const double v = unit_scale(bb, n);
-        if (v > 0x1p30 || v < 0x1p-30) {
-            u = v;
+        const int e = unit_exp(bb, n);
+        if (e > 30 || e < -30) {
+            u = std::ldexp(1.0, e);
             const bool guess = p->x_is_guess != 0;
             MGC_TRY(map(
                 n,

@@ -52,11 +52,12 @@ def test_solve_reaches_1e10(name, method, smoother, compress):
 
 
 @pytest.mark.parametrize("method,smoother,compress", [(0, 16, 12), (1, 32, 18), (2, 16, 12), (2, 32, 18), (3, 16, 12)])
-@pytest.mark.parametrize("k", [-120, 120])
+@pytest.mark.parametrize("k", [-400, -120, 120, 400])
 def test_solve_is_scale_invariant(method, smoother, compress, k):
-    """D x = b is linear: a source scaled by 2^k (rms per component near 1e-36
-    or 1e+36, so that sums of squares leave FP32's range) gives x scaled by
-    2^k, with the true residual still <= 1e-10."""
+    """D x = b is linear: a source scaled by 2^k (rms per component from 1e-120
+    to 1e+120, so that sums of squares leave FP32's range, and at +-400 the
+    square of the unit scale would leave FP64's) gives x scaled by 2^k, with
+    the true residual still <= 1e-10."""
     name = "mid_8^4"
     dims, block, eps, kappa, csw, U, psi = fields(name)
     op = _op(name, smoother, compress)
