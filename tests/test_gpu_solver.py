@@ -189,8 +189,11 @@ def test_solver_failure_modes_reported():
 
 
 @pytest.mark.parametrize("name,prec,compress,method", [("c1_16^3x32", 32, 18, 2), ("c2_32^3x64", 16, 12, 2),
-                                                      ("c2_32^3x64", 16, 12, 0)])
+                                                      ("c2_32^3x64", 16, 12, 0), ("c2_32^3x64", 16, 12, 1),
+                                                      ("c2_32^3x64", 16, 12, 3)])
 def test_full_size_solve(name, prec, compress, method):
+    """Every solver at the benchmark's size and storage (method 3 is the QWS
+    solve): the oracle recomputes D x on every site."""
     dims, block, eps, kappa, csw, U, psi = fields(name)
     op = _op(name, prec, compress)
     x, info = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=prec, method=method)
