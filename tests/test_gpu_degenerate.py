@@ -115,10 +115,13 @@ def test_zero_field_stays_zero(prec, compress):
     assert float(op.sap(z, prec=prec, n_cy=2, n_mr=3).abs().max()) == 0.0
 
 
-def test_kappa_zero_solve_returns_the_source():
-    """kappa = 0 (D = 1): the mixed solve converges, and its x is b to 1e-10."""
+@pytest.mark.parametrize("method,prec,compress", [(0, 16, 12), (1, 32, 18), (2, 16, 12), (2, 32, 18), (3, 16, 12)])
+def test_kappa_zero_solve_returns_the_source(method, prec, compress):
+    """kappa = 0 (D = 1, A = C^-1 D = 1): every solver converges, and its x is
+    b to 1e-10 (a smoother that solves every domain to its storage's precision
+    must not break the Krylov recurrences)."""
     dims, block, eps, kappa, csw, U, psi = fields("mid_8^4")
-    op = _op(dims, block, U, 0.0, csw, 16, 12)
-    x, info = op.solve(torch.from_numpy(psi).cuda(), smoother_prec=16)
+    op = _op(dims, block, U, 0.0, csw, prec, compress)
+    x, info = op.solve(torch.from_numpy(psi).cuda(), method=method, smoother_prec=prec, tol=1e-10)
     assert info.status == 0
     assert rel(x.cpu().numpy(), psi) <= 1e-10
