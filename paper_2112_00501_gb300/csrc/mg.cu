@@ -144,33 +144,62 @@ __global__ void __launch_bounds__(RWARPS * 32) k_restrict(MgGeom m, const float4
         for (int c = 0; c < 2; ++c)
 #pragma unroll
             for (int j = 0; j < CHUNK; ++j) acc[f][c][j][0] = acc[f][c][j][1] = 0.f;
-    const bool face = colq >= 0 && k >= 1;  // a coarse-operator column's face field
-    for (int d = 0; d < m.da; ++d) {
-        const int base = agg_domain(m, ac, d) << m.g.lvb;
-        for (int l = lane; l < vb; l += 32) {
-            const int i = base | l;
-            if (face) {
-                int c[4];
-                site_coords(m.g, i, c);
-                if (!on_face(m, c, k)) continue;  // the field is zero there
-            }
-            float4 vv[NCOL][6];
+    // the sums of one site
+    auto site = [&](int i) {
+        float4 vv[NCOL][6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            vv[0][q] = __ldg(plane(v, m.g, i, q));
+            if (NCOL == 2) vv[NCOL - 1][q] = __ldg(plane(v2, m.g, i, q));
+        }
+#pragma unroll
+        for (int j = 0; j < CHUNK; ++j) {
+            if (j0 + j >= m.nvec) break;
+            const float4 *w = W + (j0 + j) * fs;
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
-                vv[0][q] = __ldg(plane(v, m.g, i, q));
-                if (NCOL == 2) vv[NCOL - 1][q] = __ldg(plane(v2, m.g, i, q));
+                const float4 wq = __ldg(plane(w, m.g, i, q));
+#pragma unroll
+                for (int f = 0; f < NCOL; ++f) cdot4(acc[f][q / 3][j][0], acc[f][q / 3][j][1], wq, vv[f][q]);
             }
+        }
+    };
+    if (colq >= 0 && k >= 1) {
+        // a coarse-operator column's face field: it lives on the aggregate's
+        // last (forward hop) or first (backward hop) layer along mu, i.e. on
+        // one layer of the domains at that end; the lanes walk that layer only
+        const int mu = (k - 1) / 2;
+        const bool fwd = (k - 1) % 2 == 0;
+        const int dmu = fwd ? m.ratio[mu] - 1 : 0;
+        const int lmu = fwd ? (1 << m.g.lb[mu]) - 1 : 0;
+        const int nface = vb >> m.g.lb[mu];
+        for (int d = 0; d < m.da; ++d) {
+            int rest = d, dc = 0;
 #pragma unroll
-            for (int j = 0; j < CHUNK; ++j) {
-                if (j0 + j >= m.nvec) break;
-                const float4 *w = W + (j0 + j) * fs;
+            for (int nu = 0; nu < 4; ++nu) {
+                if (nu == mu) dc = rest % m.ratio[nu];
+                rest /= m.ratio[nu];
+            }
+            if (dc != dmu) continue;
+            const int base = agg_domain(m, ac, d) << m.g.lvb;
+            for (int t = lane; t < nface; t += 32) {
+                int lc[4], r = t;
 #pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const float4 wq = __ldg(plane(w, m.g, i, q));
-#pragma unroll
-                    for (int f = 0; f < NCOL; ++f) cdot4(acc[f][q / 3][j][0], acc[f][q / 3][j][1], wq, vv[f][q]);
+                for (int nu = 0; nu < 4; ++nu) {
+                    if (nu == mu) {
+                        lc[nu] = lmu;
+                    } else {
+                        lc[nu] = r & ((1 << m.g.lb[nu]) - 1);
+                        r >>= m.g.lb[nu];
+                    }
                 }
+                site(base | local_index(m.g, lc));
             }
+        }
+    } else {
+        for (int d = 0; d < m.da; ++d) {
+            const int base = agg_domain(m, ac, d) << m.g.lvb;
+            for (int l = lane; l < vb; l += 32) site(base | l);
         }
     }
     // butterfly sums leave every total in every lane; lane t stores sum t of
