@@ -191,7 +191,9 @@ int mgc_apply_clover(mgc_clover_t op, const void *in, void *out, int nrhs, int p
  * x_B += MR_{n_mr}(D_B, (b - D x)|_B) with D_B the Dirichlet domain operator
  * and n_mr minimal-residual steps from zero.  x (packed, prec) is updated in
  * place; x_is_zero = 1 promises x == 0 on entry and skips its first residual.
- * prec 64 computes in FP64; 32 and 16 compute in FP32.  Asynchronous.
+ * prec 64 computes in FP64; 32 and 16 compute in FP32, where a domain whose
+ * <p, p> falls below FP32's normal range takes no further MR step (alpha = 0)
+ * and an FP16-stored site below that range is stored as zero.  Asynchronous.
  */
 int mgc_sap_smooth(mgc_clover_t op, const void *b, void *x, int nrhs, int n_cy, int n_mr,
                    int prec, int x_is_zero, void *stream);
