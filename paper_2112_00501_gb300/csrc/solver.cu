@@ -1165,7 +1165,7 @@ static int residual_to32(mgc_clover_s *op, const double2 *b, const double2 *t, f
     // the product is exact and costs no FP64 instruction, unless it is so far
     // from 1 that the unscaled values could leave FP32's range
     const bool wide = scale > 0x1p90 || scale < 0x1p-90;
-    const float sf = (float)scale;
+    const float sf = wide ? 1.0f : (float)scale;  // (float) only of a value in FP32's range
     SolverWork *W = op->work;
     const Geom g = op->gauge->lat->g;
     const Spinor64 B{const_cast<double2 *>(b), g.lvb}, T{const_cast<double2 *>(t), g.lvb};
