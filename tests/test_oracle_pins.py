@@ -15,7 +15,10 @@ or finite differences:
   - dense block matrices and dense LU solves for the Dirichlet block operator,
     the minimal-residual block solve, the multiplicative SAP sweep and the
     outer solvers;
-  - central finite differences of S for the force.
+  - central finite differences of S for the force;
+  - the degenerate parameters (kappa = 0: D = 1; c_SW = 0: C = 1; a zero
+    field), where the operator, the smoother and the solve reduce to the
+    identity.
 """
 import numpy as np
 import pytest
@@ -444,3 +447,30 @@ def test_dirac_at_equals_dirac(tbc, dagger):
     idx = lambda x, y, z, t: x + Lx * (y + Ly * (z + Lz * t))  # noqa: E731
     sites = [idx(0, 0, 0, 0), idx(Lx - 1, 2, 1, Lt - 1), idx(3, Ly - 1, Lz - 1, 0), idx(1, 1, 1, 3), 7, 7]
     assert np.array_equal(O.dirac_at(dims, tbc, kappa, csw, U, psi, sites, dagger=dagger), full[sites])
+
+
+# ---------------------------------------------------------------- degenerate parameters
+
+def test_degenerate_parameters():
+    """kappa = 0 makes C = 1 and D = 1 exactly, so one MR step solves every
+    domain (p = r, alpha = 1) and one SAP sweep returns x = b, and the solve
+    returns b; c_SW = 0 makes C = 1 exactly (D = 1 - kappa H, whose hopping
+    part is pinned by the free-field and gauge-covariance tests); a zero field
+    stays zero."""
+    dims, block = (4, 4, 4, 4), (2, 2, 2, 2)
+    V = synth.volume(dims)
+    U = synth.gauge_field(dims, 0.4, synth.gauge_seed(0))
+    psi = synth.gaussian_spinor(dims, synth.source_seed(0))
+    eye = np.broadcast_to(np.eye(12, dtype=np.complex128), (V, 12, 12))
+    C0 = O.clover(dims, 0.0, 1.3, U)
+    assert np.array_equal(C0, eye)
+    assert np.array_equal(O.clover(dims, 0.13, 0.0, U), eye)
+    assert np.array_equal(O.dirac(dims, -1, 0.0, U, C0, psi), psi)
+    x = O.sap(dims, block, -1, 0.0, U, C0, psi, ncy=1, nmr=1)
+    assert np.abs(x - psi).max() <= 1e-14 * np.abs(psi).max()
+    xs, st, it, res = O.solve(dims, block, -1, 0.0, U, C0, psi, tol=1e-12)
+    assert st == 0 and np.abs(xs - psi).max() <= 1e-12 * np.abs(psi).max()
+    Cl = O.clover(dims, 0.13, 1.0, U)
+    z = np.zeros_like(psi)
+    assert np.array_equal(O.dirac(dims, -1, 0.13, U, Cl, z), z)
+    assert np.array_equal(O.sap(dims, block, -1, 0.13, U, Cl, z, ncy=2, nmr=3), z)
