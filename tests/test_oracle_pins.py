@@ -474,3 +474,36 @@ def test_degenerate_parameters():
     z = np.zeros_like(psi)
     assert np.array_equal(O.dirac(dims, -1, 0.13, U, Cl, z), z)
     assert np.array_equal(O.sap(dims, block, -1, 0.13, U, Cl, z, ncy=2, nmr=3), z)
+
+
+def test_sap_same_colour_block_order_invariance():
+    """Blocks of one colour share no hop, so a sweep does not depend on the
+    order it visits them in: a sweep composed from the pinned block MR over
+    each colour's blocks in a shuffled order (each block's residual from the
+    current x) equals the oracle's sweep, with a finite MR step count."""
+    dims, bd = (4, 4, 8, 4), (2, 2, 2, 2)
+    V = synth.volume(dims)
+    kappa = 0.13
+    U = synth.gauge_field(dims, 0.4, synth.gauge_seed(2))
+    Cl = O.clover(dims, kappa, 1.0, U)
+    b = synth.gaussian_spinor(dims, synth.source_seed(2))
+    x0 = synth.gaussian_spinor(dims, 62)
+    nb = [d // k for d, k in zip(dims, bd)]
+    blocks = [[], []]
+    for bt in range(nb[3]):
+        for bz in range(nb[2]):
+            for by in range(nb[1]):
+                for bx in range(nb[0]):
+                    blocks[(bx + by + bz + bt) % 2].append((bx, by, bz, bt))
+    rng = synth.rng(63)
+    for trial in range(2):
+        x = x0.copy()
+        for col in (0, 1):
+            order = list(blocks[col])
+            rng.shuffle(order)
+            for bc in order:
+                sites = O.block_sites(dims, bd, bc)
+                r = (b - O.dirac(dims, -1, kappa, U, Cl, x))[sites]
+                x[sites] += O.mr_block(dims, bd, bc, kappa, U, Cl, r, 3).reshape(len(sites), 4, 3)
+        want = O.sap(dims, bd, -1, kappa, U, Cl, b, x0, ncy=1, nmr=3)
+        assert np.linalg.norm(x - want) <= 1e-13 * np.linalg.norm(want), trial
