@@ -507,3 +507,33 @@ def test_sap_same_colour_block_order_invariance():
                 x[sites] += O.mr_block(dims, bd, bc, kappa, U, Cl, r, 3).reshape(len(sites), 4, 3)
         want = O.sap(dims, bd, -1, kappa, U, Cl, b, x0, ncy=1, nmr=3)
         assert np.linalg.norm(x - want) <= 1e-13 * np.linalg.norm(want), trial
+
+
+def test_force_richardson_cross_check():
+    """The force against differences at larger steps, where rounding in S is
+    negligible: central differences at h = 1e-3 and 1e-4 combined by
+    Richardson extrapolation (error O(h^4)) along random su(3) directions,
+    with the clover term on, agree with the analytic force to 1e-7."""
+    dims, bd = (4, 4, 4, 4), (2, 2, 2, 2)
+    kappa, csw, tbc = 0.125, 1.0, -1
+    U = synth.gauge_field(dims, 0.4, 81)
+    phi = synth.gaussian_spinor(dims, 82)
+    Cl = O.clover(dims, kappa, csw, U)
+    X, Y = O.force_solves(dims, bd, tbc, kappa, U, Cl, phi)
+    g = O.force(dims, tbc, kappa, csw, U, X, Y)
+    rng = synth.rng(83)
+    V = synth.volume(dims)
+    for _ in range(3):
+        site, mu = int(rng.integers(V)), int(rng.integers(4))
+        T = _su3_direction(rng)
+        w, v = np.linalg.eigh(T)
+
+        def S(hh):
+            Up = U.copy()
+            Up[site, mu] = ((v * np.exp(1j * hh * w)) @ v.conj().T) @ U[site, mu]
+            return O.action(dims, bd, tbc, kappa, csw, Up, phi)
+
+        d = {h: (S(h) - S(-h)) / (2 * h) for h in (1e-3, 1e-4)}
+        fd = (100.0 * d[1e-4] - d[1e-3]) / 99.0
+        an = np.real(np.sum(np.conj(g[site, mu]) * (1j * T @ U[site, mu])))
+        assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-3 * np.abs(g).max()), (site, mu, fd, an)
