@@ -12,7 +12,6 @@ Site s = x + Lx*(y + Ly*(z + Lz*t)).
 from __future__ import annotations
 
 import ctypes as C
-import os
 
 import numpy as np
 

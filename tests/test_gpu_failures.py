@@ -3,7 +3,6 @@ kernel gives up, reports MGC_ERR_TIMEOUT through a status word the host reads,
 and leaves the context usable."""
 import ctypes as C
 
-import numpy as np
 import pytest
 
 from helpers import TOL, fields, rel
